@@ -1,0 +1,220 @@
+/*
+ * oracle.c -- plain, slow, single-threaded CPU oracle for parametric voxel
+ * generation of 3D straight-line segments (the "Parametric Method", Section 3).
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing on the product path may call this code:
+ * only the tests, the smoke check and the CPU-baseline leg of the benchmark use
+ * it. It shares no code, header, table or helper with the CUDA library.
+ *
+ * What it computes (Section 3, Eq. (2)-(3) and the algorithm of Fig. 3):
+ *   a segment has start S and end E (integer lattice points);
+ *   N is the step count, W = (E - S) / N the step vector, and
+ *   G_k = S + W * k for k = 0, 1, ..., N are the sample points;
+ *   the voxel of G_k is the lattice point nearest to G_k on each axis.
+ *
+ * Readings where the paper is silent or garbled:
+ *   - N = max(|dx|, |dy|, |dz|) (Chebyshev length), not int(|E - S|) of Eq. (1):
+ *     this makes the major axis advance by exactly one voxel per step.
+ *   - k runs from 0 to N (Eq. (3)), so the start voxel is included: N + 1 voxels.
+ *   - N = 0 (S == E) yields the single voxel S.
+ *   - "nearest" on a tie (G_k exactly half-way between two lattice points) picks
+ *     the point farther from S.
+ *   - the arithmetic is exact: W * k is kept as the rational (E - S) * k / N.
+ *   - packed list formats: 32-bit = x | y << 10 | z << 20 (every dim <= 1024),
+ *     64-bit = x | y << 21 | z << 42; occupancy volume: bit (x + w*(y + h*z)),
+ *     little-endian bit order inside 32-bit words, OR-ed in.
+ */
+#include <stdint.h>
+#include <stddef.h>
+
+/* Status values; the numbering mirrors the public error enum on purpose so a
+ * test can compare them, but is written out here independently. */
+enum {
+    ORACLE_OK = 0,
+    ORACLE_ERR_INVALID_ARG = 1,
+    ORACLE_ERR_OUT_OF_BOUNDS = 2,
+    ORACLE_ERR_PACK_WIDTH = 3
+};
+
+static int64_t abs64(int64_t v) { return v < 0 ? -v : v; }
+
+/* N for one segment: the largest coordinate difference (Chebyshev length). */
+int64_t oracle_steps(const int32_t *seg)
+{
+    int64_t n = 0;
+    for (int a = 0; a < 3; ++a) {
+        int64_t d = abs64((int64_t)seg[3 + a] - (int64_t)seg[a]);
+        if (d > n) n = d;
+    }
+    return n;
+}
+
+/*
+ * Lattice coordinate nearest to  s + num / den  (den > 0), ties resolved away
+ * from s. With m = |num|, the distance from s in whole voxels is the integer q
+ * nearest to m / den with halves rounded up:  q = floor((2m + den) / (2 den)).
+ * Exact for every int32 input (128-bit intermediate).
+ */
+static int64_t nearest_away_from_start(int64_t s, __int128 num, int64_t den)
+{
+    __int128 m = num < 0 ? -num : num;
+    __int128 q = (2 * m + den) / (2 * (__int128)den);
+    return num < 0 ? s - (int64_t)q : s + (int64_t)q;
+}
+
+/* Voxel k of a segment: the lattice point nearest to G_k = S + W*k (Eq. (3)). */
+void oracle_voxel(const int32_t *seg, int64_t k, int64_t *out3)
+{
+    int64_t N = oracle_steps(seg);
+    for (int a = 0; a < 3; ++a) {
+        int64_t S = seg[a];
+        int64_t E = seg[3 + a];
+        if (N == 0) {
+            out3[a] = S;
+        } else {
+            /* W_a * k = (E_a - S_a) * k / N, kept as a rational */
+            __int128 num = (__int128)(E - S) * k;
+            out3[a] = nearest_away_from_start(S, num, N);
+        }
+    }
+}
+
+/* Validation of a call: dims in [1, 2^21]; every endpoint inside [0, dim);
+ * a 32-bit packed list needs every dim <= 1024. Returns the first error. */
+int oracle_validate(const int32_t *segs, int64_t n, const int32_t *dims, int want_list32)
+{
+    if (n < 0) return ORACLE_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (dims[a] < 1 || dims[a] > (1 << 21)) return ORACLE_ERR_INVALID_ARG;
+    if (want_list32)
+        for (int a = 0; a < 3; ++a)
+            if (dims[a] > 1024) return ORACLE_ERR_PACK_WIDTH;
+    for (int64_t s = 0; s < n; ++s)
+        for (int c = 0; c < 6; ++c) {
+            int32_t v = segs[6 * s + c];
+            if (v < 0 || v >= dims[c % 3]) return ORACLE_ERR_OUT_OF_BOUNDS;
+        }
+    return ORACLE_OK;
+}
+
+/* Per-segment voxel counts N + 1. */
+void oracle_count(const int32_t *segs, int64_t n, int32_t *counts)
+{
+    for (int64_t s = 0; s < n; ++s) counts[s] = (int32_t)(oracle_steps(segs + 6 * s) + 1);
+}
+
+/* Exclusive prefix sum of the counts; offsets[n] is the total voxel count V. */
+void oracle_offsets(const int32_t *counts, int64_t n, int64_t *offsets)
+{
+    int64_t run = 0;
+    for (int64_t s = 0; s < n; ++s) {
+        offsets[s] = run;
+        run += counts[s];
+    }
+    offsets[n] = run;
+}
+
+/* Fig. 3 for every segment in order: append voxel k for k = 0..N.
+ * At most `cap` words are written; the return value is V, the number the
+ * segments produce, so V > cap tells the caller the buffer was too small. */
+int64_t oracle_list32(const int32_t *segs, int64_t n, uint32_t *out, int64_t cap)
+{
+    int64_t g = 0;
+    for (int64_t s = 0; s < n; ++s) {
+        const int32_t *seg = segs + 6 * s;
+        int64_t N = oracle_steps(seg);
+        for (int64_t k = 0; k <= N; ++k) {
+            int64_t v[3];
+            oracle_voxel(seg, k, v);
+            if (g < cap)
+                out[g] = (uint32_t)v[0] | ((uint32_t)v[1] << 10) | ((uint32_t)v[2] << 20);
+            ++g;
+        }
+    }
+    return g;
+}
+
+int64_t oracle_list64(const int32_t *segs, int64_t n, uint64_t *out, int64_t cap)
+{
+    int64_t g = 0;
+    for (int64_t s = 0; s < n; ++s) {
+        const int32_t *seg = segs + 6 * s;
+        int64_t N = oracle_steps(seg);
+        for (int64_t k = 0; k <= N; ++k) {
+            int64_t v[3];
+            oracle_voxel(seg, k, v);
+            if (g < cap)
+                out[g] = (uint64_t)v[0] | ((uint64_t)v[1] << 21) | ((uint64_t)v[2] << 42);
+            ++g;
+        }
+    }
+    return g;
+}
+
+/* OR every voxel of every segment into the occupancy volume of n_words words.
+ * Returns V, or -1 if some voxel fell outside the volume (that bit is skipped). */
+int64_t oracle_bitmask(const int32_t *segs, int64_t n, const int32_t *dims, uint32_t *mask,
+                       int64_t n_words)
+{
+    int64_t w = dims[0], h = dims[1];
+    int64_t g = 0;
+    int outside = 0;
+    for (int64_t s = 0; s < n; ++s) {
+        const int32_t *seg = segs + 6 * s;
+        int64_t N = oracle_steps(seg);
+        for (int64_t k = 0; k <= N; ++k) {
+            int64_t v[3];
+            oracle_voxel(seg, k, v);
+            uint64_t lin = (uint64_t)(v[0] + w * (v[1] + h * v[2]));
+            if (lin / 32 < (uint64_t)n_words)
+                mask[lin / 32] |= (uint32_t)1 << (lin % 32);
+            else
+                outside = 1;
+            ++g;
+        }
+    }
+    return outside ? -1 : g;
+}
+
+/* Voxels of segments [s_begin, s_end) only, written as x, y, z triples; at most
+ * `cap` voxels are written, the return value is the number produced. */
+int64_t oracle_voxels_xyz(const int32_t *segs, int64_t s_begin, int64_t s_end, int64_t *xyz,
+                          int64_t cap)
+{
+    int64_t g = 0;
+    for (int64_t s = s_begin; s < s_end; ++s) {
+        const int32_t *seg = segs + 6 * s;
+        int64_t N = oracle_steps(seg);
+        for (int64_t k = 0; k <= N; ++k) {
+            if (g < cap)
+                oracle_voxel(seg, k, xyz + 3 * g);
+            ++g;
+        }
+    }
+    return g;
+}
+
+/* Number of 32-byte sectors (8 words) of the volume holding at least one set
+ * bit: with a zeroed volume before the call, the sectors a generation touched. */
+int64_t oracle_sectors_touched(const uint32_t *mask, int64_t n_words)
+{
+    int64_t touched = 0;
+    for (int64_t base = 0; base < n_words; base += 8) {
+        int any = 0;
+        for (int64_t j = base; j < base + 8 && j < n_words; ++j)
+            if (mask[j]) any = 1;
+        touched += any;
+    }
+    return touched;
+}
+
+/* Set-bit count of the volume (number of distinct occupied voxels). */
+int64_t oracle_popcount(const uint32_t *mask, int64_t n_words)
+{
+    int64_t c = 0;
+    for (int64_t j = 0; j < n_words; ++j) {
+        uint32_t x = mask[j];
+        while (x) { x &= x - 1; ++c; }
+    }
+    return c;
+}
