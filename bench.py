@@ -1,0 +1,370 @@
+#!/usr/bin/env python3
+"""Benchmark of the voxelization hot path on GB300.
+
+One step = one pass of the whole path over the fixed-length batch workload
+(1,048,576 segments of 64 voxels plus one 1023-step segment in a 1024^3
+volume; the Table 3 shape, plus Table 2's single segment): count + decoupled
+look-back scan, then voxel-parallel generation writing the packed 32-bit list
+and OR-ing the 1-bit occupancy volume. Inputs are resident in HBM; L2 is
+flushed (a 256 MiB write) between timed steps, outside the step's events.
+
+Prints ONE JSON line (rank 0). ``--impl reference`` times the CPU oracle on the
+host cores instead (a bounded sample of the same workload per step).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "voxels/s (bit-exact) & % HBM roofline, batched vs plain launch; p99 ms"
+UNIT = "voxels/s"
+WORKLOAD = "fixed-length batch: 1,048,576 segments x 64 voxels + one 1023-step segment, 1024^3 volume, list32 + 1-bit volume"
+L2_FLUSH_BYTES = 256 << 20
+SM_CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                   "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                   "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def _kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2009_09500_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()[:16]
+
+
+def _recorded_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from a committed ncu summary, if it was
+    taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    ent = rec.get(kernel)
+    if not ent or ent.get("source_hash") != _kernel_source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={SM_CLOCK_FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _cpu_cores_used() -> int:
+    return 1  # the oracle is single-threaded
+
+
+def cpu_oracle_rate(segs: np.ndarray, dims, max_seconds: float = 12.0):
+    """The oracle as it stands (list32 + volume) on a bounded sample of the
+    workload: whole segments from the front until ~max_seconds of CPU work."""
+    import oracle
+
+    O = oracle.get()
+    n = segs.shape[0]
+    chunk = 65536
+    done_s = 0
+    vox_done = 0
+    t_total = 0.0
+    mask = np.zeros(O.mask_words(dims), dtype=np.uint32)
+    while done_s < n and t_total < max_seconds:
+        part = segs[done_s:done_s + chunk]
+        t0 = time.perf_counter()
+        lst = O.list32(part)
+        O.bitmask(part, dims, mask)
+        t_total += time.perf_counter() - t0
+        vox_done += len(lst)
+        done_s += part.shape[0]
+    return {"value": vox_done / t_total, "unit": UNIT, "cores": _cpu_cores_used(), "kind": "oracle",
+            "sample": f"first {done_s} of {n} segments ({vox_done} voxels), list32 + volume, one pass, "
+                      f"{t_total:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return 0
+    from paper_2009_09500_gb300 import workloads
+    import oracle
+
+    w = workloads.config2()
+    O = oracle.get()
+    per_step = 16384  # segments per step: a bounded sample (~1M voxels)
+    times = []
+    vox_per = []
+    mask = np.zeros(O.mask_words(w.dims), dtype=np.uint32)
+    for it in range(args.warmup + args.steps):
+        lo = (it * per_step) % (w.n - per_step)
+        part = w.segs[lo:lo + per_step]
+        t0 = time.perf_counter()
+        lst = O.list32(part)
+        O.bitmask(part, w.dims, mask)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+            vox_per.append(len(lst))
+    total_t = sum(times)
+    value = sum(vox_per) / total_t
+    sample = f"{per_step} consecutive segments per step (~{int(np.mean(vox_per))} voxels), list32 + volume"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * total_t / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "segments": w.n, "volume": list(w.dims),
+                   "note": "CPU oracle (plain single-threaded C), each step a bounded sample of the workload"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2009_09500_gb300 import build, vox, workloads
+
+    rank, world, local = _dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    build.build_library()
+    vox.load()
+
+    # each rank voxelizes its own fixed-length batch (independent problems: weak scaling)
+    w = workloads.config2(seed=1 + 1000 * rank)
+    n = w.n
+    stream = torch.cuda.current_stream()
+    segs = torch.from_numpy(w.segs).to(dev)
+    ws = torch.empty(vox.vox_workspace_size(n), dtype=torch.uint8, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    offsets = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    vox.vox_count(segs, w.dims, ws, status, None, offsets)
+    torch.cuda.synchronize()
+    V = int(offsets[-1].item())
+    assert int(status.item()) == 0
+    lst = torch.empty(V, dtype=torch.int32, device=dev)
+    words = vox.vox_mask_words(w.dims)
+    mask = torch.zeros(words, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    flags = vox.OUT_LIST32 | vox.OUT_BITMASK
+
+    def step(ev0=None, ev1=None, ev2=None):
+        if ev0 is not None:
+            ev0.record(stream)
+        vox.vox_count(segs, w.dims, ws, status, None, None, stream)
+        if ev1 is not None:
+            ev1.record(stream)
+        vox.vox_generate_from_scan(segs, w.dims, ws, status, lst, mask, flags, stream)
+        if ev2 is not None:
+            ev2.record(stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if int(status.item()) != 0:
+        raise RuntimeError(f"device status {vox.strerror(int(status.item()))}")
+    # bytes the volume read-modify-writes: 64 B per distinct 32-byte sector touched
+    sectors = int((mask.view(-1, 8) != 0).any(dim=1).sum().item()) if words % 8 == 0 else None
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(dev.index if dev.index is not None else 0)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        step(*evs[k])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    st = int(status.item())
+    if st != 0:
+        raise RuntimeError(f"device status {vox.strerror(st)}")
+    step_ms = [a.elapsed_time(c) for a, b, c in evs]
+    scan_ms = [a.elapsed_time(b) for a, b, c in evs]
+    gen_ms = [b.elapsed_time(c) for a, b, c in evs]
+    ms_mean = float(np.mean(step_ms))
+    if world > 1:
+        t = torch.tensor([ms_mean], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_mean_max = float(t.item())
+    else:
+        ms_mean_max = ms_mean
+    total_voxels = V * world
+    value = total_voxels / (ms_mean_max / 1000.0)
+
+    # roofline of the dominant kernel (generation): algorithmic bytes per launch
+    peaks, peak_kind = _measured_peaks()
+    gen_mean = float(np.mean(gen_ms))
+    alg_bytes = 24 * n + 4 * V + (64 * sectors if sectors is not None else 0)
+    achieved = alg_bytes / (gen_mean / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                "frac": achieved / float(peaks["hbm_gbs"]), "traffic": _recorded_traffic("k_generate"),
+                "kernel": "k_generate<16, list32|mask>", "peak_kind": f"{peak_kind} HBM copy",
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "bytes_model": "24 B/segment read + 4 B/voxel list + 64 B per distinct 32-B volume sector"}
+
+    # end to end through the host-buffer entry point (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        h_segs = torch.from_numpy(w.segs).pin_memory()
+        h_list = torch.empty(V, dtype=torch.int32).pin_memory()
+        h_mask = torch.empty(words, dtype=torch.int32).pin_memory()
+        arena = torch.empty(vox.vox_host_arena_size(n, w.dims, flags, V), dtype=torch.uint8, device=dev)
+        for _ in range(2):
+            vox.vox_generate_host(h_segs, w.dims, arena, h_list, h_mask, flags, stream)
+        reps = max(3, min(20, args.steps))
+        e2e_t = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            ta = time.perf_counter()
+            got = vox.vox_generate_host(h_segs, w.dims, arena, h_list, h_mask, flags, stream)
+            e2e_t.append(time.perf_counter() - ta)
+            assert got == V
+        e2e_s = float(np.median(e2e_t))
+        e2e = {"value": total_voxels / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 24 * n,
+               "d2h_bytes_per_step": 4 * V + 4 * words + 8 + 4 + 4, "ms": 1000 * e2e_s,
+               "note": "vox_generate_host: pinned host segments in, list + volume out, median of "
+                       f"{reps} synchronous calls"}
+        del arena
+
+    if rank != 0:
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_rate(w.segs, w.dims, args.cpu_seconds)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_mean_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "segments": n, "voxels_per_gpu": V, "volume": list(w.dims),
+                   "outputs": "list32 + bitmask", "launch": "plain (count+scan, generate) on one stream",
+                   "l2": "flushed between steps by a 256 MiB write (outside the step events)",
+                   "parallelism": f"replicas x{world} (independent batches)"},
+        "segments_per_s": n * world / (ms_mean_max / 1000.0),
+        "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+        "kernels_ms": {"count_scan": float(np.mean(scan_ms)), "generate": gen_mean},
+        "wall_s_timed_region": wall,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "gpu_launches": 2 * args.steps,
+        "gpu_launches_note": "k_count_scan + k_generate per step (plus 2 memset nodes)",
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

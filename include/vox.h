@@ -1,0 +1,177 @@
+/*
+ * vox.h -- C ABI of libvox, a GB300 (sm_103a) library for parametric voxel
+ * generation of 3D straight-line segments.
+ *
+ * The operation (Section 3 of "3D Primitives GPGPU Generation for Volume
+ * Visualization in 3D Graphics Systems", Eq. (2)-(3) and Fig. 3):
+ *   a segment from S = (x0, y0, z0) to E = (x1, y1, z1) (integer endpoints) has
+ *   N = max(|x1 - x0|, |y1 - y0|, |z1 - z0|) steps and N + 1 voxels; voxel k
+ *   (k = 0..N) is the lattice point nearest to G_k = S + (E - S) k / N on each
+ *   axis, a coordinate exactly half-way between two integers going to the one
+ *   farther from S. In integers, per axis a with d_a = E_a - S_a:
+ *     q_a(k) = floor((2 k |d_a| + N) / (2 N)),  v_a(k) = S_a + sign(d_a) q_a(k).
+ *   N = 0 gives the single voxel S. All arithmetic is exact.
+ *
+ * Outputs (all optional, any combination; OR the VOX_OUT_* flags):
+ *   VOX_OUT_LIST32   uint32 per voxel: x | y << 10 | z << 20   (every dim <= 1024)
+ *   VOX_OUT_LIST64   uint64 per voxel: x | y << 21 | z << 42
+ *   VOX_OUT_BITMASK  occupancy volume, one bit per voxel: voxel (x, y, z) is bit
+ *                    b = x + w*(y + h*z), i.e. bit (b % 32) of uint32 word b / 32;
+ *                    ceil(w*h*d / 32) words. Bits are OR-ed in: the caller clears
+ *                    the volume when it wants a fresh one.
+ *   The list holds the voxels of segment 0 (k = 0..N), then segment 1, and so on:
+ *   voxel k of segment s sits at index offsets[s] + k, offsets being the exclusive
+ *   prefix sum of the per-segment counts N + 1. Voxels shared by two segments
+ *   appear twice in a list and once in the volume.
+ *
+ * Conventions for every call:
+ *   - Pointers named d_* or documented as "device" are CUDA device pointers on
+ *     the current device; h_* are host pointers. The caller allocates and owns
+ *     every buffer; the library allocates nothing and keeps no state between
+ *     calls except a per-device cache of launch limits.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*; NULL
+ *     means the legacy default stream) unless documented otherwise, and never
+ *     synchronise the device.
+ *   - Errors the host can see (bad pointer, size, flag, alignment, workspace too
+ *     small) are returned at once and nothing is launched. Errors found on the
+ *     device are written to *d_status (a device int32 that the call first sets
+ *     to VOX_OK); the first error wins. Once *d_status holds an error, the
+ *     generation kernels of that call write nothing at all (list and volume are
+ *     left untouched). Read *d_status after synchronising the stream.
+ *   - Segment arrays are vox_segment[n] (24 bytes each, int32), device memory,
+ *     16-byte aligned. Every endpoint must lie in [0, dim) of its axis, and
+ *     every dim in [1, 2^21].
+ */
+#ifndef VOX_H
+#define VOX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum vox_status {
+    VOX_OK = 0,
+    VOX_ERR_INVALID_ARG = 1,   /* NULL pointer, n < 0, bad flags, dims outside [1, 2^21] */
+    VOX_ERR_OUT_OF_BOUNDS = 2, /* (device) an endpoint lies outside [0, dim) */
+    VOX_ERR_PACK_WIDTH = 3,    /* LIST32 requested with a dim above 1024 */
+    VOX_ERR_CAPACITY = 4,      /* (device) list capacity below the total voxel count */
+    VOX_ERR_TIMEOUT = 5,       /* (device) a bounded wait inside a kernel expired */
+    VOX_ERR_CUDA = 6,          /* a CUDA runtime call or launch failed */
+    VOX_ERR_WORKSPACE = 7,     /* workspace NULL, too small or not 256-byte aligned */
+    VOX_ERR_ALIGNMENT = 8      /* segments not 16-byte aligned, list/volume misaligned */
+} vox_status;
+
+typedef struct vox_segment {
+    int32_t x0, y0, z0; /* start point S */
+    int32_t x1, y1, z1; /* end point E */
+} vox_segment;
+
+typedef struct vox_dims {
+    int32_t w, h, d; /* volume extent along x, y, z, in voxels */
+} vox_dims;
+
+#define VOX_OUT_LIST32 1
+#define VOX_OUT_LIST64 2
+#define VOX_OUT_BITMASK 4
+
+/* Bytes of workspace a call on n segments needs (count, scan and generation of
+ * one scene). The workspace is device memory, 256-byte aligned, caller-owned,
+ * and may be reused by the next call on the same stream. */
+size_t vox_workspace_size(int64_t n_segments);
+
+/*
+ * vox_count -- per-segment voxel counts N + 1 and their exclusive prefix sum
+ * (the preprocessing of Section 4, step 1, and the lengths N_i of the
+ * multi-segment case). Validates every endpoint against dims.
+ *   d_segs     device vox_segment[n], 16-byte aligned
+ *   n          number of segments (0 allowed)
+ *   dims       volume extent (each in [1, 2^21])
+ *   d_counts   device int32[n] receiving N + 1, or NULL
+ *   d_offsets  device int64[n + 1] receiving the exclusive prefix sum, with the
+ *              total voxel count V in d_offsets[n], or NULL
+ *   d_ws       workspace of vox_workspace_size(n) bytes; it also keeps the
+ *              offsets for a following vox_generate_from_scan
+ *   d_status   device int32, set to VOX_OK then to the first device error
+ *   stream     cudaStream_t as void*
+ */
+vox_status vox_count(const vox_segment *d_segs, int64_t n, vox_dims dims,
+                     int32_t *d_counts, int64_t *d_offsets,
+                     void *d_ws, size_t ws_bytes, int32_t *d_status, void *stream);
+
+/*
+ * vox_generate -- the whole method on one scene: counts, exclusive scan, then
+ * every voxel of every segment (Fig. 3 for all segments at once, Section 4),
+ * written to the requested outputs.
+ *   d_segs, n, dims  as for vox_count
+ *   d_list           device list (uint32 for LIST32, uint64 for LIST64; 16-byte
+ *                    aligned) or NULL when no list flag is set
+ *   list_capacity    elements available in d_list; V above it is
+ *                    VOX_ERR_CAPACITY (device) and nothing is written
+ *   d_mask           device uint32[ceil(w*h*d/32)], 4-byte aligned, OR-ed into;
+ *                    NULL when VOX_OUT_BITMASK is not set
+ *   flags            VOX_OUT_LIST32 or VOX_OUT_LIST64 (not both), optionally
+ *                    | VOX_OUT_BITMASK; at least one output
+ *   d_ws, ws_bytes   workspace of at least vox_workspace_size(n) bytes
+ *   d_status         as for vox_count
+ */
+vox_status vox_generate(const vox_segment *d_segs, int64_t n, vox_dims dims,
+                        void *d_list, int64_t list_capacity, uint32_t *d_mask, int flags,
+                        void *d_ws, size_t ws_bytes, int32_t *d_status, void *stream);
+
+/*
+ * vox_generate_from_scan -- the generation step alone, reusing the counts and
+ * offsets that a preceding vox_count left in d_ws for the same d_segs, n and
+ * dims, on the same stream. Does not reset *d_status: an error found by that
+ * vox_count keeps this call from writing anything. Arguments as for
+ * vox_generate.
+ */
+vox_status vox_generate_from_scan(const vox_segment *d_segs, int64_t n, vox_dims dims,
+                                  void *d_list, int64_t list_capacity, uint32_t *d_mask,
+                                  int flags, void *d_ws, size_t ws_bytes, int32_t *d_status,
+                                  void *stream);
+
+/*
+ * vox_generate_host -- vox_generate on host buffers, copies included (the
+ * host-device pipeline of Fig. 4: input copy, kernels, result copy back).
+ * SYNCHRONOUS: returns once the results are in host memory (it synchronises
+ * `stream` twice: once to learn V, once at the end).
+ *   h_segs          host vox_segment[n] (pinned memory for full copy speed)
+ *   h_list          host list of list_capacity elements, or NULL
+ *   h_mask          host uint32[ceil(w*h*d/32)], OVERWRITTEN with the volume of
+ *                   these segments alone (not OR-ed), or NULL
+ *   d_arena         device scratch of vox_host_arena_size(...) bytes, 256-byte aligned
+ *   h_total         receives V (may be NULL)
+ *   returns         VOX_OK or the first error, host or device
+ */
+size_t vox_host_arena_size(int64_t n, vox_dims dims, int flags, int64_t list_capacity);
+vox_status vox_generate_host(const vox_segment *h_segs, int64_t n, vox_dims dims,
+                             void *h_list, int64_t list_capacity, uint32_t *h_mask, int flags,
+                             void *d_arena, size_t arena_bytes, int64_t *h_total, void *stream);
+
+/* Human-readable name of a status code. Never NULL. */
+const char *vox_strerror(int status);
+
+/* Number of 32-bit words of the occupancy volume for dims (ceil(w*h*d / 32)). */
+int64_t vox_mask_words(vox_dims dims);
+
+/*
+ * Test hook for failure detection: when tile >= 0, the next count/scan launches
+ * make scan tile `tile` skip publishing its prefix, so the tile after it meets
+ * the bounded wait of the decoupled look-back, gives up after wait_ns
+ * nanoseconds, and reports VOX_ERR_TIMEOUT in *d_status instead of hanging.
+ * tile < 0 turns the hook off. wait_ns <= 0 restores the default limit.
+ * Process-wide; not for production use.
+ */
+void vox_debug_set_scan_stall(int64_t tile, int64_t wait_ns);
+
+/* Segments per scan tile of the count/scan kernel (for tests that aim the hook). */
+int64_t vox_scan_tile_segments(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VOX_H */

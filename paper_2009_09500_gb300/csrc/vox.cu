@@ -1,0 +1,338 @@
+// vox.cu -- the C ABI of libvox (declared in include/vox.h): argument checks,
+// workspace layout, kernel selection and launches. Host code only calls the
+// CUDA runtime for launches, stream-ordered memsets/copies and device queries;
+// it allocates no device memory.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
+
+#include "vox.h"
+#include "vox_kernels.cuh"
+
+namespace {
+
+using namespace vox;
+
+constexpr size_t kWsAlign = 256;
+constexpr int64_t kMaxDim = int64_t(1) << 21;
+constexpr int kRun = 16;                      // voxels per thread run in k_generate
+constexpr int64_t kMinPerCta = 2048;          // smallest voxel range given to one CTA
+constexpr int64_t kDefaultWaitNs = 500000000;  // 0.5 s bound on every in-kernel wait
+
+std::atomic<int64_t> g_stall_tile{-1};
+std::atomic<int64_t> g_wait_ns{kDefaultWaitNs};
+
+size_t align_up(size_t x) { return (x + kWsAlign - 1) & ~(kWsAlign - 1); }
+
+struct WsLayout {
+    int64_t n_tiles;
+    size_t desc;     // uint64 [n_tiles]; the ticket sits at byte 0
+    size_t offsets;  // int64 [n + 4]
+    size_t total;
+};
+
+WsLayout ws_layout(int64_t n)
+{
+    WsLayout L;
+    L.n_tiles = (n + kScanTile - 1) / kScanTile;
+    L.desc = kWsAlign;
+    L.offsets = L.desc + align_up(sizeof(uint64_t) * static_cast<size_t>(L.n_tiles > 0 ? L.n_tiles : 1));
+    L.total = L.offsets + align_up(sizeof(int64_t) * static_cast<size_t>(n + 4));
+    return L;
+}
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
+vox_status check_dims(vox_dims dims)
+{
+    if (dims.w < 1 || dims.h < 1 || dims.d < 1) return VOX_ERR_INVALID_ARG;
+    if (dims.w > kMaxDim || dims.h > kMaxDim || dims.d > kMaxDim) return VOX_ERR_INVALID_ARG;
+    return VOX_OK;
+}
+
+uint64_t volume_bits(vox_dims d)
+{
+    return static_cast<uint64_t>(d.w) * static_cast<uint64_t>(d.h) * static_cast<uint64_t>(d.d);
+}
+
+int sm_count()
+{
+    static std::mutex mu;
+    static std::map<int, int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(dev);
+    if (it != cache.end()) return it->second;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    cache[dev] = sms;
+    return sms;
+}
+
+int blocks_per_sm(const void *kernel, int threads, size_t smem)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    std::lock_guard<std::mutex> lock(mu);
+    auto key = std::make_pair(kernel, dev);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, smem) != cudaSuccess) return 0;
+    cache[key] = b;
+    return b;
+}
+
+// Host-side checks shared by the generation entry points.
+vox_status check_generate_args(const vox_segment *segs, int64_t n, vox_dims dims, const void *list,
+                               int64_t capacity, const uint32_t *mask, int flags, const void *ws,
+                               size_t ws_bytes, const int32_t *status)
+{
+    if (n < 0 || status == nullptr) return VOX_ERR_INVALID_ARG;
+    if (n > 0 && segs == nullptr) return VOX_ERR_INVALID_ARG;
+    if (vox_status e = check_dims(dims)) return e;
+    if (flags & ~(VOX_OUT_LIST32 | VOX_OUT_LIST64 | VOX_OUT_BITMASK)) return VOX_ERR_INVALID_ARG;
+    const bool l32 = flags & VOX_OUT_LIST32, l64 = flags & VOX_OUT_LIST64, bm = flags & VOX_OUT_BITMASK;
+    if (!(l32 || l64 || bm) || (l32 && l64)) return VOX_ERR_INVALID_ARG;
+    if (l32 && (dims.w > 1024 || dims.h > 1024 || dims.d > 1024)) return VOX_ERR_PACK_WIDTH;
+    if ((l32 || l64) && (list == nullptr || capacity < 0)) return VOX_ERR_INVALID_ARG;
+    if (bm && mask == nullptr) return VOX_ERR_INVALID_ARG;
+    if (n > 0 && !aligned(segs, 16)) return VOX_ERR_ALIGNMENT;
+    if ((l32 || l64) && !aligned(list, 16)) return VOX_ERR_ALIGNMENT;
+    if (bm && !aligned(mask, 4)) return VOX_ERR_ALIGNMENT;
+    if (ws == nullptr || !aligned(ws, kWsAlign) || ws_bytes < ws_layout(n).total) return VOX_ERR_WORKSPACE;
+    return VOX_OK;
+}
+
+vox_status launch_count_scan(const vox_segment *segs, int64_t n, vox_dims dims, int32_t *counts,
+                             int64_t *offsets_out, void *ws, int32_t *status, cudaStream_t stream)
+{
+    const WsLayout L = ws_layout(n);
+    char *base = static_cast<char *>(ws);
+    if (cudaMemsetAsync(base, 0, L.offsets, stream) != cudaSuccess) return VOX_ERR_CUDA;
+    ScanParams p;
+    p.segs = reinterpret_cast<const int32_t *>(segs);
+    p.n = n;
+    p.w = dims.w;
+    p.h = dims.h;
+    p.d = dims.d;
+    p.counts = counts;
+    p.offsets = reinterpret_cast<int64_t *>(base + L.offsets);
+    p.offsets_out = offsets_out;
+    p.desc = reinterpret_cast<uint64_t *>(base + L.desc);
+    p.ticket = reinterpret_cast<uint32_t *>(base);
+    p.status = status;
+    p.n_tiles = L.n_tiles;
+    p.stall_tile = g_stall_tile.load();
+    p.wait_ns = static_cast<uint64_t>(g_wait_ns.load());
+    k_count_scan<<<static_cast<unsigned>(L.n_tiles), kScanThreads, 0, stream>>>(p);
+    return cudaGetLastError() == cudaSuccess ? VOX_OK : VOX_ERR_CUDA;
+}
+
+template <int OUT, bool LIN64>
+vox_status launch_gen_t(const GenParams &p, cudaStream_t stream)
+{
+    auto kernel = k_generate<kRun, OUT, LIN64>;
+    const size_t smem = sizeof(GenSmem<kRun>);
+    const int per_sm = blocks_per_sm(reinterpret_cast<const void *>(kernel), kGenThreads, smem);
+    const int sms = sm_count();
+    if (per_sm <= 0 || sms <= 0) return VOX_ERR_CUDA;
+    kernel<<<static_cast<unsigned>(per_sm * sms), kGenThreads, smem, stream>>>(p);
+    return cudaGetLastError() == cudaSuccess ? VOX_OK : VOX_ERR_CUDA;
+}
+
+vox_status launch_generate(const vox_segment *segs, int64_t n, vox_dims dims, void *list, int64_t capacity,
+                           uint32_t *mask, int flags, void *ws, int32_t *status, cudaStream_t stream)
+{
+    if (n == 0) return VOX_OK;
+    const WsLayout L = ws_layout(n);
+    GenParams p;
+    p.segs = reinterpret_cast<const int32_t *>(segs);
+    p.n = n;
+    p.offsets = reinterpret_cast<const int64_t *>(static_cast<char *>(ws) + L.offsets);
+    p.w = dims.w;
+    p.h = dims.h;
+    p.d = dims.d;
+    p.list = list;
+    p.capacity = capacity;
+    p.mask = mask;
+    p.status = status;
+    p.wait_ns = static_cast<uint64_t>(g_wait_ns.load());
+    p.min_per_cta = kMinPerCta;
+    const bool lin64 = volume_bits(dims) > (uint64_t(1) << 32);
+    const bool bm = flags & VOX_OUT_BITMASK;
+    if (flags & VOX_OUT_LIST32) {
+        return bm ? launch_gen_t<kOutList32 | kOutMask, false>(p, stream) : launch_gen_t<kOutList32, false>(p, stream);
+    }
+    if (flags & VOX_OUT_LIST64) {
+        if (!bm) return launch_gen_t<kOutList64, false>(p, stream);
+        return lin64 ? launch_gen_t<kOutList64 | kOutMask, true>(p, stream)
+                     : launch_gen_t<kOutList64 | kOutMask, false>(p, stream);
+    }
+    return lin64 ? launch_gen_t<kOutMask, true>(p, stream) : launch_gen_t<kOutMask, false>(p, stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t vox_workspace_size(int64_t n_segments)
+{
+    if (n_segments < 0) return 0;
+    return ws_layout(n_segments).total;
+}
+
+int64_t vox_scan_tile_segments(void) { return kScanTile; }
+
+int64_t vox_mask_words(vox_dims dims)
+{
+    if (check_dims(dims) != VOX_OK) return 0;
+    return static_cast<int64_t>((volume_bits(dims) + 31) / 32);
+}
+
+vox_status vox_count(const vox_segment *d_segs, int64_t n, vox_dims dims, int32_t *d_counts, int64_t *d_offsets,
+                     void *d_ws, size_t ws_bytes, int32_t *d_status, void *stream)
+{
+    if (n < 0 || d_status == nullptr || (n > 0 && d_segs == nullptr)) return VOX_ERR_INVALID_ARG;
+    if (vox_status e = check_dims(dims)) return e;
+    if (n > 0 && !aligned(d_segs, 16)) return VOX_ERR_ALIGNMENT;
+    if (d_ws == nullptr || !aligned(d_ws, kWsAlign) || ws_bytes < ws_layout(n).total) return VOX_ERR_WORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), s) != cudaSuccess) return VOX_ERR_CUDA;
+    if (n == 0) {
+        const WsLayout L = ws_layout(0);
+        if (cudaMemsetAsync(static_cast<char *>(d_ws) + L.offsets, 0, 4 * sizeof(int64_t), s) != cudaSuccess)
+            return VOX_ERR_CUDA;
+        if (d_offsets && cudaMemsetAsync(d_offsets, 0, sizeof(int64_t), s) != cudaSuccess) return VOX_ERR_CUDA;
+        return VOX_OK;
+    }
+    return launch_count_scan(d_segs, n, dims, d_counts, d_offsets, d_ws, d_status, s);
+}
+
+vox_status vox_generate(const vox_segment *d_segs, int64_t n, vox_dims dims, void *d_list, int64_t list_capacity,
+                        uint32_t *d_mask, int flags, void *d_ws, size_t ws_bytes, int32_t *d_status, void *stream)
+{
+    if (vox_status e = check_generate_args(d_segs, n, dims, d_list, list_capacity, d_mask, flags, d_ws, ws_bytes,
+                                           d_status))
+        return e;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), s) != cudaSuccess) return VOX_ERR_CUDA;
+    if (n == 0) return VOX_OK;
+    if (vox_status e = launch_count_scan(d_segs, n, dims, nullptr, nullptr, d_ws, d_status, s)) return e;
+    return launch_generate(d_segs, n, dims, d_list, list_capacity, d_mask, flags, d_ws, d_status, s);
+}
+
+vox_status vox_generate_from_scan(const vox_segment *d_segs, int64_t n, vox_dims dims, void *d_list,
+                                  int64_t list_capacity, uint32_t *d_mask, int flags, void *d_ws, size_t ws_bytes,
+                                  int32_t *d_status, void *stream)
+{
+    if (vox_status e = check_generate_args(d_segs, n, dims, d_list, list_capacity, d_mask, flags, d_ws, ws_bytes,
+                                           d_status))
+        return e;
+    return launch_generate(d_segs, n, dims, d_list, list_capacity, d_mask, flags, d_ws, d_status,
+                           static_cast<cudaStream_t>(stream));
+}
+
+size_t vox_host_arena_size(int64_t n, vox_dims dims, int flags, int64_t list_capacity)
+{
+    if (n < 0 || list_capacity < 0 || check_dims(dims) != VOX_OK) return 0;
+    const size_t elem = (flags & VOX_OUT_LIST64) ? 8 : ((flags & VOX_OUT_LIST32) ? 4 : 0);
+    size_t total = align_up(sizeof(int32_t));                                   // status
+    total += align_up(sizeof(vox_segment) * static_cast<size_t>(n));            // segments
+    total += align_up(elem * static_cast<size_t>(list_capacity));               // list
+    if (flags & VOX_OUT_BITMASK) total += align_up(4 * static_cast<size_t>(vox_mask_words(dims)));
+    total += ws_layout(n).total;                                                // workspace
+    return total;
+}
+
+vox_status vox_generate_host(const vox_segment *h_segs, int64_t n, vox_dims dims, void *h_list,
+                             int64_t list_capacity, uint32_t *h_mask, int flags, void *d_arena, size_t arena_bytes,
+                             int64_t *h_total, void *stream)
+{
+    if (n < 0 || (n > 0 && h_segs == nullptr)) return VOX_ERR_INVALID_ARG;
+    if (vox_status e = check_dims(dims)) return e;
+    const bool has_list = flags & (VOX_OUT_LIST32 | VOX_OUT_LIST64);
+    const bool bm = flags & VOX_OUT_BITMASK;
+    if ((has_list && h_list == nullptr) || (bm && h_mask == nullptr)) return VOX_ERR_INVALID_ARG;
+    const size_t need = vox_host_arena_size(n, dims, flags, list_capacity);
+    if (d_arena == nullptr || !aligned(d_arena, kWsAlign) || need == 0 || arena_bytes < need) return VOX_ERR_WORKSPACE;
+    const size_t elem = (flags & VOX_OUT_LIST64) ? 8 : ((flags & VOX_OUT_LIST32) ? 4 : 0);
+    char *a = static_cast<char *>(d_arena);
+    int32_t *d_status = reinterpret_cast<int32_t *>(a);
+    a += align_up(sizeof(int32_t));
+    vox_segment *d_segs = reinterpret_cast<vox_segment *>(a);
+    a += align_up(sizeof(vox_segment) * static_cast<size_t>(n));
+    void *d_list = has_list ? a : nullptr;
+    a += align_up(elem * static_cast<size_t>(list_capacity));
+    uint32_t *d_mask = nullptr;
+    const int64_t words = vox_mask_words(dims);
+    if (bm) {
+        d_mask = reinterpret_cast<uint32_t *>(a);
+        a += align_up(4 * static_cast<size_t>(words));
+    }
+    void *d_ws = a;
+    const size_t ws_bytes = ws_layout(n).total;
+    if (vox_status e = check_generate_args(n > 0 ? d_segs : nullptr, n, dims, d_list, list_capacity, d_mask, flags,
+                                           d_ws, ws_bytes, d_status))
+        return e;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (n > 0 && cudaMemcpyAsync(d_segs, h_segs, sizeof(vox_segment) * static_cast<size_t>(n),
+                                 cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return VOX_ERR_CUDA;
+    if (vox_status e = vox_count(d_segs, n, dims, nullptr, nullptr, d_ws, ws_bytes, d_status, s)) return e;
+    int64_t V = 0;
+    int32_t st = 0;
+    const WsLayout L = ws_layout(n);
+    if (cudaMemcpyAsync(&V, static_cast<char *>(d_ws) + L.offsets + sizeof(int64_t) * static_cast<size_t>(n),
+                        sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return VOX_ERR_CUDA;
+    if (cudaMemcpyAsync(&st, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return VOX_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return VOX_ERR_CUDA;
+    if (h_total) *h_total = V;
+    if (st != VOX_OK) return static_cast<vox_status>(st);
+    if (has_list && V > list_capacity) return VOX_ERR_CAPACITY;
+    if (bm && cudaMemsetAsync(d_mask, 0, 4 * static_cast<size_t>(words), s) != cudaSuccess) return VOX_ERR_CUDA;
+    if (vox_status e = launch_generate(d_segs, n, dims, d_list, list_capacity, d_mask, flags, d_ws, d_status, s))
+        return e;
+    if (has_list && V > 0 &&
+        cudaMemcpyAsync(h_list, d_list, elem * static_cast<size_t>(V), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return VOX_ERR_CUDA;
+    if (bm && cudaMemcpyAsync(h_mask, d_mask, 4 * static_cast<size_t>(words), cudaMemcpyDeviceToHost, s) !=
+                  cudaSuccess)
+        return VOX_ERR_CUDA;
+    if (cudaMemcpyAsync(&st, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return VOX_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return VOX_ERR_CUDA;
+    return static_cast<vox_status>(st);
+}
+
+const char *vox_strerror(int status)
+{
+    switch (status) {
+    case VOX_OK: return "ok";
+    case VOX_ERR_INVALID_ARG: return "invalid argument";
+    case VOX_ERR_OUT_OF_BOUNDS: return "segment endpoint outside the volume";
+    case VOX_ERR_PACK_WIDTH: return "32-bit list needs every volume edge <= 1024";
+    case VOX_ERR_CAPACITY: return "list capacity below the total voxel count";
+    case VOX_ERR_TIMEOUT: return "bounded in-kernel wait expired";
+    case VOX_ERR_CUDA: return "CUDA runtime error";
+    case VOX_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case VOX_ERR_ALIGNMENT: return "buffer misaligned (segments and lists need 16 bytes)";
+    default: return "unknown status";
+    }
+}
+
+void vox_debug_set_scan_stall(int64_t tile, int64_t wait_ns)
+{
+    g_stall_tile.store(tile < 0 ? -1 : tile);
+    g_wait_ns.store(wait_ns > 0 ? wait_ns : kDefaultWaitNs);
+}
+
+}  // extern "C"

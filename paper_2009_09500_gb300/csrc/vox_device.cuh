@@ -1,0 +1,240 @@
+// vox_device.cuh -- device-side building blocks of libvox (sm_103a).
+//
+// Small inline-PTX wrappers (global timer, relaxed 64-bit accesses, mbarrier,
+// 1-D TMA bulk copy global -> shared) and the per-segment stepping state used by
+// the generation kernels.
+//
+// The stepping state implements Eq. (3) of the paper (G_k = S + W k, W = (E - S)/N)
+// with the nearest-lattice rounding done exactly in integers. Per axis a with
+// A = |d_a| the voxel offset from S is q(k) = floor((2 k A + N) / (2 N)); the
+// remainder r(k) = (2 k A + N) mod 2N then advances by 2A per step and gives back
+// 2N, moving the voxel one step along sign(d_a), each time it reaches 2N (A <= N,
+// so at most once per step). One division per axis enters a segment mid-way
+// (Section 3: voxel k does not depend on voxel k - 1); every further voxel costs
+// an add and a compare per minor axis.
+#pragma once
+
+#include <cstdint>
+
+namespace vox {
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t *p)
+{
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed_u64(uint64_t *p, uint64_t v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ int32_t ld_volatile_i32(const int32_t *p)
+{
+    return *reinterpret_cast<const volatile int32_t *>(p);
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of an mbarrier, giving up after limit_ns nanoseconds.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (globaltimer_ns() - t0 > limit_ns) return false;
+    }
+    return true;
+}
+
+// 1-D TMA bulk copy global -> this CTA's shared memory; completion is counted in
+// bytes on `bar`. dst, src and bytes must be multiples of 16.
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void set_status(int32_t *status, int32_t code)
+{
+    atomicCAS(status, 0, code);
+}
+
+// ------------------------------------------------------- per-segment stepping
+// Voxel offset q and remainder r of one axis at step k (0 <= k <= N, N > 0):
+// q = floor((2 k A + N) / (2 N)), r = (2 k A + N) - 2 N q.
+__device__ __forceinline__ void axis_entry(int32_t A, int32_t N, int32_t k, int32_t &q, int32_t &r)
+{
+    if (A == N) {  // the numerator is N (mod 2N) for every k
+        q = k;
+        r = N;
+    } else if (A == 0) {
+        q = 0;
+        r = N;
+    } else if (N <= 46340) {  // 2 N^2 + N < 2^32: 32-bit unsigned division is exact
+        const uint32_t num = 2u * static_cast<uint32_t>(k) * static_cast<uint32_t>(A) + static_cast<uint32_t>(N);
+        const uint32_t den = 2u * static_cast<uint32_t>(N);
+        const uint32_t qq = num / den;
+        q = static_cast<int32_t>(qq);
+        r = static_cast<int32_t>(num - qq * den);
+    } else {
+        const uint64_t num = 2ull * static_cast<uint64_t>(k) * static_cast<uint64_t>(A) + static_cast<uint64_t>(N);
+        const uint64_t den = 2ull * static_cast<uint64_t>(N);
+        const uint64_t qq = num / den;
+        q = static_cast<int32_t>(qq);
+        r = static_cast<int32_t>(num - qq * den);
+    }
+}
+
+// Output encodings of a voxel (x, y, z).
+template <typename PackT>
+__device__ __forceinline__ PackT pack_unit(int axis);
+
+template <>
+__device__ __forceinline__ uint32_t pack_unit<uint32_t>(int axis)
+{
+    return 1u << (10 * axis);
+}
+
+template <>
+__device__ __forceinline__ uint64_t pack_unit<uint64_t>(int axis)
+{
+    return 1ull << (21 * axis);
+}
+
+// Signed step of `unit` along an axis whose delta is d (+unit, -unit or 0),
+// in two's complement so that adding it to a packed word moves one field.
+template <typename T>
+__device__ __forceinline__ T signed_step(int32_t d, T unit)
+{
+    return d > 0 ? unit : (d < 0 ? static_cast<T>(T(0) - unit) : T(0));
+}
+
+// Stepping state of one segment. PackT: uint32_t (LIST32) or uint64_t (LIST64);
+// LinT: uint32_t or uint64_t volume bit index (volumes up to or beyond 2^32 bits).
+template <typename PackT, typename LinT>
+struct Stepper {
+    int32_t left;     // steps still to take inside this segment (N - k)
+    int32_t twoN;     // 2N
+    int32_t Ab2, Ac2; // 2|d| of the two minor axes
+    int32_t rb, rc;   // their remainders
+    PackT P, dPm, dPb, dPc;
+    LinT L, dLm, dLb, dLc;
+
+    // Enter segment (x0, y0, z0) -> (x1, y1, z1) at step k.
+    __device__ __forceinline__ void enter(const int32_t *rec, int32_t k, LinT w, LinT wh)
+    {
+        const int32_t x0 = rec[0], y0 = rec[1], z0 = rec[2];
+        const int32_t dx = rec[3] - x0, dy = rec[4] - y0, dz = rec[5] - z0;
+        const int32_t ax = abs(dx), ay = abs(dy), az = abs(dz);
+        const int32_t N = max(ax, max(ay, az));
+        left = N - k;
+        twoN = 2 * N;
+        int32_t qx = 0, qy = 0, qz = 0, rx = N, ry = N, rz = N;
+        if (N > 0) {
+            axis_entry(ax, N, k, qx, rx);
+            axis_entry(ay, N, k, qy, ry);
+            axis_entry(az, N, k, qz, rz);
+        }
+        const int32_t vx = x0 + (dx >= 0 ? qx : -qx);
+        const int32_t vy = y0 + (dy >= 0 ? qy : -qy);
+        const int32_t vz = z0 + (dz >= 0 ? qz : -qz);
+        P = static_cast<PackT>(vx) | (static_cast<PackT>(vy) * pack_unit<PackT>(1)) |
+            (static_cast<PackT>(vz) * pack_unit<PackT>(2));
+        L = static_cast<LinT>(vx) + static_cast<LinT>(vy) * w + static_cast<LinT>(vz) * wh;
+        // major axis: the first with |d| = N; minors b, c are the other two in order
+        const bool mx = (ax == N);
+        const bool my = !mx && (ay == N);
+        const int32_t dm = mx ? dx : (my ? dy : dz);
+        const int32_t db = mx ? dy : dx;
+        const int32_t dc = (mx || my) ? dz : dy;
+        const int axis_m = mx ? 0 : (my ? 1 : 2);
+        const int axis_b = mx ? 1 : 0;
+        const int axis_c = (mx || my) ? 2 : 1;
+        Ab2 = 2 * abs(db);
+        Ac2 = 2 * abs(dc);
+        rb = mx ? ry : rx;
+        rc = (mx || my) ? rz : ry;
+        dPm = signed_step<PackT>(dm, pack_unit<PackT>(axis_m));
+        dPb = signed_step<PackT>(db, pack_unit<PackT>(axis_b));
+        dPc = signed_step<PackT>(dc, pack_unit<PackT>(axis_c));
+        const LinT um = axis_m == 0 ? LinT(1) : (axis_m == 1 ? w : wh);
+        const LinT ub = axis_b == 0 ? LinT(1) : w;
+        const LinT uc = axis_c == 2 ? wh : w;
+        dLm = signed_step<LinT>(dm, um);
+        dLb = signed_step<LinT>(db, ub);
+        dLc = signed_step<LinT>(dc, uc);
+    }
+
+    // One step along the segment (requires left > 0).
+    __device__ __forceinline__ void step()
+    {
+        --left;
+        P += dPm;
+        L += dLm;
+        rb += Ab2;
+        if (rb >= twoN) {
+            rb -= twoN;
+            P += dPb;
+            L += dLb;
+        }
+        rc += Ac2;
+        if (rc >= twoN) {
+            rc -= twoN;
+            P += dPc;
+            L += dLc;
+        }
+    }
+};
+
+}  // namespace vox

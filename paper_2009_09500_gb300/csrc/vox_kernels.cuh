@@ -1,0 +1,407 @@
+// vox_kernels.cuh -- the three kernels of the voxelization hot path (sm_103a):
+//
+//   k_count_scan  per-segment voxel count N + 1 (+ endpoint validation) fused
+//                 with a single-pass decoupled look-back exclusive scan
+//                 (Merrill & Garland, 2016) into int64 offsets;
+//   k_generate    voxel-parallel generation: each CTA owns a contiguous range of
+//                 global voxel ids, stages windows of segment records and offsets
+//                 into shared memory with 1-D TMA bulk copies, maps each thread's
+//                 run of R voxels back to (segment, k) by a search in the staged
+//                 offsets, and steps through the run with the exact integer
+//                 recurrence, writing packed coordinates and/or OR-ing bits.
+//
+// The paper's multi-segment kernel pads every segment to N_max threads (Section 5,
+// Fig. 4b) and names the resulting divergence as its main loss for segments of
+// arbitrary length; the scan plus the voxel-range split here give every CTA the
+// same number of voxels whatever the length mix.
+#pragma once
+
+#include <cstdint>
+#include <type_traits>
+
+#include "vox_device.cuh"
+
+namespace vox {
+
+__device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;  // segments per scan tile
+
+constexpr uint64_t kDescAgg = 1ull << 62;  // tile aggregate published
+constexpr uint64_t kDescInc = 2ull << 62;  // tile inclusive prefix published
+constexpr uint64_t kDescValue = (1ull << 62) - 1;
+
+constexpr int kGenThreads = 256;
+constexpr int kWindowSegs = 1024;  // segment records staged per window (even)
+
+// Status codes written by the kernels (same values as the public vox_status).
+constexpr int32_t kStOutOfBounds = 2;
+constexpr int32_t kStCapacity = 4;
+constexpr int32_t kStTimeout = 5;
+
+struct ScanParams {
+    const int32_t *segs;  // [n][6]
+    int64_t n;
+    int32_t w, h, d;
+    int32_t *counts;       // [n] or null
+    int64_t *offsets;      // [n + 4] workspace copy (entry n = total, then padding)
+    int64_t *offsets_out;  // [n + 1] caller copy or null
+    uint64_t *desc;        // [n_tiles] tile descriptors, zeroed before launch
+    uint32_t *ticket;      // dynamic tile counter, zeroed before launch
+    int32_t *status;
+    int64_t n_tiles;
+    int64_t stall_tile;  // test hook: this tile publishes nothing (-1: off)
+    uint64_t wait_ns;    // bound of every wait
+};
+
+// ---------------------------------------------------------------- count + scan
+__global__ void __launch_bounds__(kScanThreads) k_count_scan(ScanParams p)
+{
+    __shared__ __align__(16) int32_t s_cnt[kScanTile];
+    __shared__ int64_t s_loc[kScanTile];
+    __shared__ int64_t s_warp[kScanThreads / 32];
+    __shared__ int64_t s_excl;
+    __shared__ int64_t s_total;
+    __shared__ uint32_t s_tile;
+
+    const int t = threadIdx.x;
+    const int lane = t & 31;
+    const int warp = t >> 5;
+    if (t == 0) s_tile = atomicAdd(p.ticket, 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t base = tile * kScanTile;
+
+    // counts, read in a strided (coalesced) order
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        const int idx = j * kScanThreads + t;
+        const int64_t s = base + idx;
+        int32_t c = 0;
+        if (s < p.n) {
+            const int2 *r = reinterpret_cast<const int2 *>(p.segs + 6 * s);
+            const int2 a = __ldg(r), b = __ldg(r + 1), e = __ldg(r + 2);
+            const int32_t x0 = a.x, y0 = a.y, z0 = b.x, x1 = b.y, y1 = e.x, z1 = e.y;
+            const bool ok = (unsigned)x0 < (unsigned)p.w && (unsigned)x1 < (unsigned)p.w &&
+                            (unsigned)y0 < (unsigned)p.h && (unsigned)y1 < (unsigned)p.h &&
+                            (unsigned)z0 < (unsigned)p.d && (unsigned)z1 < (unsigned)p.d;
+            if (ok) {
+                c = max(abs(x1 - x0), max(abs(y1 - y0), abs(z1 - z0))) + 1;
+            } else {
+                bad = true;
+                c = 1;
+            }
+            if (p.counts) p.counts[s] = c;
+        }
+        s_cnt[idx] = c;
+    }
+    if (bad) set_status(p.status, kStOutOfBounds);
+    __syncthreads();
+
+    // blocked exclusive scan: thread t owns segments 8t .. 8t+7 of the tile
+    int32_t v[kScanItems];
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(s_cnt + kScanItems * t);
+        const int4 u0 = src[0], u1 = src[1];
+        v[0] = u0.x; v[1] = u0.y; v[2] = u0.z; v[3] = u0.w;
+        v[4] = u1.x; v[5] = u1.y; v[6] = u1.z; v[7] = u1.w;
+    }
+    int32_t ex[kScanItems];
+    int32_t run = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        ex[k] = run;
+        run += v[k];
+    }
+    int64_t inc = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    int64_t warp_base = 0, total = 0;
+#pragma unroll
+    for (int wi = 0; wi < kScanThreads / 32; ++wi) {
+        const int64_t sw = s_warp[wi];
+        if (wi < warp) warp_base += sw;
+        total += sw;
+    }
+    const int64_t thread_excl = warp_base + inc - run;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) s_loc[kScanItems * t + k] = thread_excl + ex[k];
+
+    // decoupled look-back by warp 0
+    if (warp == 0) {
+        const bool stall = (tile == p.stall_tile);
+        int64_t excl = 0;
+        if (tile == 0) {
+            if (lane == 0 && !stall) st_relaxed_u64(p.desc, kDescInc | static_cast<uint64_t>(total));
+        } else {
+            if (lane == 0 && !stall) st_relaxed_u64(p.desc + tile, kDescAgg | static_cast<uint64_t>(total));
+            int64_t look = tile - 1;
+            uint64_t t0 = 0;
+            bool timed_out = false;
+            while (true) {
+                const int64_t idx = look - lane;
+                const uint64_t dv = idx >= 0 ? ld_relaxed_u64(p.desc + idx) : kDescInc;
+                const uint32_t flag = static_cast<uint32_t>(dv >> 62);
+                const uint32_t inc_mask = __ballot_sync(0xffffffffu, flag == 2u);
+                const uint32_t zero_mask = __ballot_sync(0xffffffffu, flag == 0u);
+                const int first_inc = inc_mask ? __ffs(inc_mask) - 1 : 32;
+                const uint32_t need = first_inc >= 31 ? 0xffffffffu : ((2u << first_inc) - 1u);
+                if (zero_mask & need) {
+                    // a predecessor has not published yet: spin, within a bound (the
+                    // clock is read by lane 0 so that the whole warp decides alike)
+                    const uint64_t now = __shfl_sync(0xffffffffu, globaltimer_ns(), 0);
+                    if (t0 == 0) t0 = now;
+                    if (now - t0 <= p.wait_ns) {
+                        __nanosleep(64);
+                        continue;
+                    }
+                    timed_out = true;
+                    if (lane == 0) set_status(p.status, kStTimeout);
+                }
+                int64_t part = (lane <= first_inc && flag != 0u) ? static_cast<int64_t>(dv & kDescValue) : 0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+                excl += part;
+                if (first_inc < 32 || timed_out) break;
+                look -= 32;
+                t0 = 0;
+            }
+            if (lane == 0 && !stall) st_relaxed_u64(p.desc + tile, kDescInc | static_cast<uint64_t>(excl + total));
+        }
+        if (lane == 0) {
+            s_excl = excl;
+            s_total = total;
+        }
+    }
+    __syncthreads();
+
+    const int64_t excl = s_excl;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        const int idx = j * kScanThreads + t;
+        const int64_t s = base + idx;
+        if (s < p.n) {
+            const int64_t o = excl + s_loc[idx];
+            p.offsets[s] = o;
+            if (p.offsets_out) p.offsets_out[s] = o;
+        }
+    }
+    if (tile == p.n_tiles - 1 && t == 0) {
+        const int64_t V = excl + s_total;
+        p.offsets[p.n] = V;
+        // padding entries: even-sized bulk copies of the offsets may read them
+        p.offsets[p.n + 1] = V;
+        p.offsets[p.n + 2] = V;
+        p.offsets[p.n + 3] = V;
+        if (p.offsets_out) p.offsets_out[p.n] = V;
+    }
+}
+
+// ------------------------------------------------------------------ generation
+enum : int { kOutList32 = 1, kOutList64 = 2, kOutMask = 4 };
+
+struct GenParams {
+    const int32_t *segs;     // [n][6], 16-byte aligned
+    int64_t n;
+    const int64_t *offsets;  // [n + 4], 16-byte aligned (workspace)
+    int32_t w, h, d;
+    void *list;              // uint32 / uint64 list or null
+    int64_t capacity;
+    uint32_t *mask;          // volume or null
+    int32_t *status;
+    uint64_t wait_ns;
+    int64_t min_per_cta;     // smallest voxel range worth a CTA (multiple of 4)
+};
+
+template <int R>
+struct GenSmem {
+    uint64_t bar;
+    int64_t V;
+    int64_t offs[kWindowSegs + 2];
+    int32_t recs[kWindowSegs * 6];
+    int32_t go;
+};
+
+// Largest s in [lo, hi) with offsets[s] <= g, given offsets[lo] <= g < offsets[hi]:
+// a 256-ary search where each round every thread probes one position. Must be
+// called by all threads of the CTA with the same arguments.
+__device__ __forceinline__ int64_t find_segment_block(const int64_t *offsets, int64_t lo, int64_t hi, int64_t g)
+{
+    while (hi - lo > 1) {
+        const int64_t span = hi - lo;
+        const int64_t stride = (span + kGenThreads - 1) / kGenThreads;
+        const int64_t pos = lo + static_cast<int64_t>(threadIdx.x) * stride;
+        const bool le = pos < hi && __ldg(offsets + pos) <= g;
+        const int cnt = __syncthreads_count(le);  // probes 0 .. cnt-1 satisfy (monotone)
+        const int64_t nlo = lo + static_cast<int64_t>(cnt - 1) * stride;
+        const int64_t nhi = min(hi, lo + static_cast<int64_t>(cnt) * stride);
+        lo = nlo;
+        hi = nhi;
+    }
+    return lo;
+}
+
+// Largest j in [0, cnt) with offs[j] <= g (offs[0] <= g < offs[cnt]); cnt <= kWindowSegs.
+__device__ __forceinline__ int32_t find_in_window(const int64_t *offs, int32_t cnt, int64_t g)
+{
+    int32_t lo = 0;
+#pragma unroll
+    for (int32_t step = kWindowSegs / 2; step > 0; step >>= 1) {
+        const int32_t m = lo + step;
+        if (m < cnt && offs[m] <= g) lo = m;
+    }
+    return lo;
+}
+
+template <int R, int OUT, bool LIN64>
+__global__ void __launch_bounds__(kGenThreads) k_generate(GenParams p)
+{
+    using PackT = typename std::conditional<(OUT & kOutList64) != 0, uint64_t, uint32_t>::type;
+    using LinT = typename std::conditional<LIN64, uint64_t, uint32_t>::type;
+    constexpr bool kList = (OUT & (kOutList32 | kOutList64)) != 0;
+    constexpr bool kMask = (OUT & kOutMask) != 0;
+    constexpr int kPass = kGenThreads * R;
+    static_assert(R % 4 == 0, "runs must keep 16-byte store alignment");
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    GenSmem<R> &sm = *reinterpret_cast<GenSmem<R> *>(smem_raw);
+    const int t = threadIdx.x;
+
+    // prologue decided by one thread so that the whole CTA agrees
+    if (t == 0) {
+        int32_t go = ld_volatile_i32(p.status) == 0;  // an earlier error: write nothing
+        const int64_t V = __ldg(p.offsets + p.n);
+        if (go && kList && V > p.capacity) {
+            set_status(p.status, kStCapacity);
+            go = 0;
+        }
+        sm.V = V;
+        sm.go = go;
+        mbar_init(&sm.bar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (!sm.go) return;
+    const int64_t V = sm.V;
+    // contiguous voxel range of this CTA, a multiple of 4 long
+    int64_t per = (V + gridDim.x - 1) / gridDim.x;
+    per = max(per, p.min_per_cta);
+    per = (per + 3) & ~int64_t(3);
+    const int64_t gA = static_cast<int64_t>(blockIdx.x) * per;
+    if (gA >= V) return;
+    const int64_t gB = min(gA + per, V);
+
+    uint32_t phase = 0;
+    int64_t s_cur = find_segment_block(p.offsets, 0, p.n, gA);
+
+    const LinT w = static_cast<LinT>(p.w);
+    const LinT wh = static_cast<LinT>(p.w) * static_cast<LinT>(p.h);
+    int64_t g0 = gA;
+    while (g0 < gB) {
+        // ---- stage a window of segment records and offsets (TMA bulk copies)
+        const int64_t s_base = s_cur & ~int64_t(1);
+        const int32_t cnt = static_cast<int32_t>(min64(kWindowSegs, p.n - s_base));
+        const int32_t cnt_bulk = cnt & ~1;             // 24 * even bytes is a multiple of 16
+        const int32_t off_entries = (cnt + 3) & ~1;    // entries s_base .. s_base+cnt (+1 pad), even
+        __syncthreads();  // previous window fully consumed
+        if (t == 0) {
+            fence_proxy_async_smem();
+            const uint32_t rec_bytes = static_cast<uint32_t>(cnt_bulk) * 24u;
+            const uint32_t off_bytes = static_cast<uint32_t>(off_entries) * 8u;
+            mbar_arrive_expect_tx(&sm.bar, rec_bytes + off_bytes);
+            if (rec_bytes) bulk_copy_g2s(sm.recs, p.segs + 6 * s_base, rec_bytes, &sm.bar);
+            bulk_copy_g2s(sm.offs, p.offsets + s_base, off_bytes, &sm.bar);
+        }
+        if (cnt != cnt_bulk && t < 6) sm.recs[6 * cnt_bulk + t] = __ldg(p.segs + 6 * (s_base + cnt_bulk) + t);
+        const bool landed = mbar_wait_bounded(&sm.bar, phase, p.wait_ns);
+        phase ^= 1u;
+        if (__syncthreads_or(!landed)) {
+            // a copy did not land in time: report, give it one more bounded wait, stop
+            if (t == 0) set_status(p.status, kStTimeout);
+            if (landed == false) mbar_wait_bounded(&sm.bar, phase ^ 1u, p.wait_ns);
+            return;
+        }
+
+        const int64_t win_end = sm.offs[cnt];  // first voxel after the window's segments
+        int64_t g_end = gB;
+        if (win_end < gB) g_end = win_end & ~int64_t(3);
+
+        // ---- passes over [g0, g_end), R consecutive voxels per thread
+        for (int64_t gp = g0; gp < g_end; gp += kPass) {
+            const int64_t g = gp + static_cast<int64_t>(t) * R;
+            if (g < g_end) {
+                const int32_t len = static_cast<int32_t>(min64(R, g_end - g));
+                int32_t j = find_in_window(sm.offs, cnt, g);
+                Stepper<PackT, LinT> st;
+                st.enter(sm.recs + 6 * j, static_cast<int32_t>(g - sm.offs[j]), w, wh);
+                PackT out[R];
+                LinT cur_word = static_cast<LinT>(~LinT(0));
+                uint32_t acc = 0;
+#pragma unroll
+                for (int u = 0; u < R; ++u) {
+                    if (u < len) {
+                        if (kList) out[u] = st.P;
+                        if (kMask) {
+                            const LinT word = st.L >> 5;
+                            const uint32_t bit = 1u << (static_cast<uint32_t>(st.L) & 31u);
+                            if (word == cur_word) {
+                                acc |= bit;
+                            } else {
+                                if (acc) atomicOr(p.mask + cur_word, acc);
+                                cur_word = word;
+                                acc = bit;
+                            }
+                        }
+                        if (u + 1 < len) {
+                            if (st.left == 0) {
+                                ++j;
+                                st.enter(sm.recs + 6 * j, 0, w, wh);
+                            } else {
+                                st.step();
+                            }
+                        }
+                    }
+                }
+                if (kMask && acc) atomicOr(p.mask + cur_word, acc);
+                if (kList) {
+                    PackT *dst = static_cast<PackT *>(p.list) + g;
+                    if (len == R) {
+                        constexpr int kPerVec = 16 / sizeof(PackT);
+#pragma unroll
+                        for (int u = 0; u < R; u += kPerVec) {
+                            if constexpr (sizeof(PackT) == 4) {
+                                uint4 q;
+                                q.x = static_cast<uint32_t>(out[u]);
+                                q.y = static_cast<uint32_t>(out[u + 1]);
+                                q.z = static_cast<uint32_t>(out[u + 2]);
+                                q.w = static_cast<uint32_t>(out[u + 3]);
+                                *reinterpret_cast<uint4 *>(dst + u) = q;
+                            } else {
+                                ulonglong2 q;
+                                q.x = static_cast<unsigned long long>(out[u]);
+                                q.y = static_cast<unsigned long long>(out[u + 1]);
+                                *reinterpret_cast<ulonglong2 *>(dst + u) = q;
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < R; ++u)
+                            if (u < len) dst[u] = out[u];
+                    }
+                }
+            }
+        }
+        g0 = g_end;
+        if (g0 < gB) s_cur = (g0 >= win_end) ? s_base + cnt : s_base + find_in_window(sm.offs, cnt, g0);
+    }
+}
+
+}  // namespace vox

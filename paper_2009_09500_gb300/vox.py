@@ -1,0 +1,271 @@
+"""Python binding of libvox (include/vox.h): argument marshalling only.
+
+Every step of the voxelization runs in the CUDA kernels of ``libvox.so``; this
+module turns torch tensors into pointers, picks the current CUDA stream, and
+raises on a non-OK status. There is no CPU fallback: if the library is missing
+the import of a function fails loudly.
+
+Names follow the C ABI: ``vox_count``, ``vox_generate``,
+``vox_generate_from_scan``, ``vox_generate_host``, ``vox_workspace_size``,
+``vox_mask_words``, ``vox_strerror``.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK = 0
+ERR_INVALID_ARG = 1
+ERR_OUT_OF_BOUNDS = 2
+ERR_PACK_WIDTH = 3
+ERR_CAPACITY = 4
+ERR_TIMEOUT = 5
+ERR_CUDA = 6
+ERR_WORKSPACE = 7
+ERR_ALIGNMENT = 8
+
+OUT_LIST32 = 1
+OUT_LIST64 = 2
+OUT_BITMASK = 4
+
+EXPORTED = (
+    "vox_workspace_size", "vox_count", "vox_generate", "vox_generate_from_scan",
+    "vox_host_arena_size", "vox_generate_host", "vox_strerror", "vox_mask_words",
+    "vox_debug_set_scan_stall", "vox_scan_tile_segments",
+)
+
+
+class Dims(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_int32), ("h", ctypes.c_int32), ("d", ctypes.c_int32)]
+
+
+class VoxError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        self.status = int(status)
+        super().__init__(f"{where}: {strerror(status)} (status {status})")
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libvox.so (never builds implicitly; call build.build_library())."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    path = path or _build.LIB
+    try:  # load torch's CUDA runtime first so that libvox shares it (same current device)
+        import torch  # noqa: F401
+    except ImportError:
+        pass
+    if not os.path.exists(path):
+        raise RuntimeError(f"libvox.so not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    vp, i64, i32, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_size_t
+    lib.vox_workspace_size.argtypes = [i64]
+    lib.vox_workspace_size.restype = sz
+    lib.vox_count.argtypes = [vp, i64, Dims, vp, vp, vp, sz, vp, vp]
+    lib.vox_count.restype = i32
+    for name in ("vox_generate", "vox_generate_from_scan"):
+        f = getattr(lib, name)
+        f.argtypes = [vp, i64, Dims, vp, i64, vp, i32, vp, sz, vp, vp]
+        f.restype = i32
+    lib.vox_host_arena_size.argtypes = [i64, Dims, i32, i64]
+    lib.vox_host_arena_size.restype = sz
+    lib.vox_generate_host.argtypes = [vp, i64, Dims, vp, i64, vp, i32, vp, sz, vp, vp]
+    lib.vox_generate_host.restype = i32
+    lib.vox_strerror.argtypes = [i32]
+    lib.vox_strerror.restype = ctypes.c_char_p
+    lib.vox_mask_words.argtypes = [Dims]
+    lib.vox_mask_words.restype = i64
+    lib.vox_debug_set_scan_stall.argtypes = [i64, i64]
+    lib.vox_debug_set_scan_stall.restype = None
+    lib.vox_scan_tile_segments.argtypes = []
+    lib.vox_scan_tile_segments.restype = i64
+    if path == _build.LIB:
+        _lib = lib
+    return lib
+
+
+def strerror(status: int) -> str:
+    return load().vox_strerror(int(status)).decode()
+
+
+def _dims(dims) -> Dims:
+    w, h, d = (int(v) for v in dims)
+    return Dims(w, h, d)
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    if t is None:
+        return ctypes.c_void_p(0)
+    return ctypes.c_void_p(int(t.data_ptr()))
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+def _check(st: int, where: str):
+    if st != OK:
+        raise VoxError(st, where)
+
+
+def vox_workspace_size(n: int) -> int:
+    return int(load().vox_workspace_size(int(n)))
+
+
+def vox_mask_words(dims) -> int:
+    return int(load().vox_mask_words(_dims(dims)))
+
+
+def vox_strerror(status: int) -> str:
+    return strerror(status)
+
+
+def vox_scan_tile_segments() -> int:
+    return int(load().vox_scan_tile_segments())
+
+
+def vox_debug_set_scan_stall(tile: int, wait_ns: int = 0) -> None:
+    load().vox_debug_set_scan_stall(int(tile), int(wait_ns))
+
+
+def _check_segs(segs):
+    import torch
+
+    if not (segs.is_cuda and segs.dtype == torch.int32 and segs.dim() == 2 and segs.shape[1] == 6
+            and segs.is_contiguous()):
+        raise ValueError("segments must be a contiguous CUDA int32 tensor of shape [n, 6]")
+
+
+def vox_count(segs, dims, ws, status, counts=None, offsets=None, stream=None) -> None:
+    """Launch the count + scan on ``stream``; raises on host-side errors only
+    (device errors land in ``status``)."""
+    _check_segs(segs)
+    st = load().vox_count(_ptr(segs), segs.shape[0], _dims(dims), _ptr(counts), _ptr(offsets),
+                          _ptr(ws), ws.numel() * ws.element_size(), _ptr(status), _stream(stream))
+    _check(st, "vox_count")
+
+
+def _gen(fn, segs, dims, ws, status, list_out=None, mask=None, flags=None, stream=None, capacity=None):
+    import torch
+
+    _check_segs(segs)
+    if flags is None:
+        flags = 0
+        if list_out is not None:
+            flags |= OUT_LIST64 if list_out.dtype in (torch.int64, torch.uint64) else OUT_LIST32
+        if mask is not None:
+            flags |= OUT_BITMASK
+    cap = int(capacity if capacity is not None else (list_out.numel() if list_out is not None else 0))
+    st = fn(_ptr(segs), segs.shape[0], _dims(dims), _ptr(list_out), cap, _ptr(mask), int(flags),
+            _ptr(ws), ws.numel() * ws.element_size(), _ptr(status), _stream(stream))
+    return st
+
+
+def vox_generate(segs, dims, ws, status, list_out=None, mask=None, flags=None, stream=None, capacity=None):
+    """Count, scan and generate on ``stream`` (asynchronous). ``list_out``: int32
+    tensor for the 32-bit list or int64 for the 64-bit list; ``mask``: int32
+    tensor of vox_mask_words(dims) words, OR-ed into."""
+    st = _gen(load().vox_generate, segs, dims, ws, status, list_out, mask, flags, stream, capacity)
+    _check(st, "vox_generate")
+
+
+def vox_generate_from_scan(segs, dims, ws, status, list_out=None, mask=None, flags=None, stream=None,
+                           capacity=None):
+    st = _gen(load().vox_generate_from_scan, segs, dims, ws, status, list_out, mask, flags, stream, capacity)
+    _check(st, "vox_generate_from_scan")
+
+
+def vox_host_arena_size(n: int, dims, flags: int, capacity: int) -> int:
+    return int(load().vox_host_arena_size(int(n), _dims(dims), int(flags), int(capacity)))
+
+
+def vox_generate_host(h_segs, dims, arena, h_list=None, h_mask=None, flags=None, stream=None):
+    """Synchronous host-buffer variant: copies in, generates, copies out.
+    h_segs / h_list / h_mask are CPU tensors (pinned for speed). Returns V."""
+    import torch
+
+    if not (h_segs.dtype == torch.int32 and h_segs.dim() == 2 and h_segs.shape[1] == 6
+            and h_segs.is_contiguous() and not h_segs.is_cuda):
+        raise ValueError("h_segs must be a contiguous CPU int32 tensor of shape [n, 6]")
+    if flags is None:
+        flags = 0
+        if h_list is not None:
+            flags |= OUT_LIST64 if h_list.dtype in (torch.int64, torch.uint64) else OUT_LIST32
+        if h_mask is not None:
+            flags |= OUT_BITMASK
+    cap = h_list.numel() if h_list is not None else 0
+    total = ctypes.c_int64(0)
+    st = load().vox_generate_host(_ptr(h_segs), h_segs.shape[0], _dims(dims), _ptr(h_list), cap, _ptr(h_mask),
+                                  int(flags), _ptr(arena), arena.numel() * arena.element_size(),
+                                  ctypes.byref(total), _stream(stream))
+    _check(st, "vox_generate_host")
+    return int(total.value)
+
+
+# ------------------------------------------------------------------ conveniences
+class Voxelizer:
+    """Owns a reusable workspace and status word on one device (torch-allocated),
+    and allocates outputs on request. Thin: every call goes to the C ABI."""
+
+    def __init__(self, max_segments: int, device=None):
+        import torch
+
+        self.device = torch.device(device or "cuda")
+        self.max_segments = int(max_segments)
+        self.ws = torch.empty(vox_workspace_size(self.max_segments), dtype=torch.uint8, device=self.device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=self.device)
+
+    def _fit(self, n: int):
+        if n > self.max_segments:
+            import torch
+
+            self.max_segments = n
+            self.ws = torch.empty(vox_workspace_size(n), dtype=torch.uint8, device=self.device)
+
+    def count(self, segs, dims, stream=None):
+        """Returns (counts int32[n], offsets int64[n+1]) as device tensors."""
+        import torch
+
+        n = segs.shape[0]
+        self._fit(n)
+        counts = torch.empty(n, dtype=torch.int32, device=self.device)
+        offsets = torch.empty(n + 1, dtype=torch.int64, device=self.device)
+        vox_count(segs, dims, self.ws, self.status, counts, offsets, stream)
+        return counts, offsets
+
+    def total(self, segs, dims) -> int:
+        _, off = self.count(segs, dims)
+        self.raise_status()
+        return int(off[-1].item())
+
+    def generate(self, segs, dims, list_out=None, mask=None, flags=None, stream=None):
+        self._fit(segs.shape[0])
+        vox_generate(segs, dims, self.ws, self.status, list_out, mask, flags, stream)
+
+    def raise_status(self):
+        st = int(self.status.item())
+        if st != OK:
+            raise VoxError(st, "device")
+
+
+def segments_tensor(segs_np: np.ndarray, device="cuda"):
+    import torch
+
+    a = np.ascontiguousarray(segs_np, dtype=np.int32)
+    return torch.from_numpy(a).to(device)

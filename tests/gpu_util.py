@@ -1,0 +1,103 @@
+"""Helpers shared by the GPU tests: run the CUDA path through the C ABI and
+compare with the oracle. Oracle outputs are computed here on the CPU from the
+same input bytes; nothing the CUDA path produces feeds the oracle."""
+
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+import oracle
+from paper_2009_09500_gb300 import vox
+
+SENTINEL32 = -0x21524111  # 0xDEADBEEF as int32
+SENTINEL64 = -0x2152411021524111
+
+
+def run_gpu(segs_np, dims, flags, capacity=None, extra=64, mask_init=None, use_from_scan=False):
+    """vox_count then vox_generate (or vox_generate_from_scan) on cuda:0.
+    The list gets ``extra`` sentinel elements past the capacity the call is told
+    about, to catch writes beyond it."""
+    segs = torch.from_numpy(np.ascontiguousarray(segs_np, dtype=np.int32)).cuda()
+    n = segs.shape[0]
+    ws = torch.empty(vox.vox_workspace_size(n), dtype=torch.uint8, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    counts = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+    offsets = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    vox.vox_count(segs, dims, ws, status, counts[:n] if n else None, offsets)
+    torch.cuda.synchronize()
+    count_status = int(status.item())
+    V = int(offsets[-1].item())
+    if capacity is None:
+        capacity = V
+    res = {"count_status": count_status, "V": V, "counts": counts[:n].cpu().numpy(),
+           "offsets": offsets.cpu().numpy(), "capacity": capacity}
+    list_t = None
+    if flags & vox.OUT_LIST64:
+        list_t = torch.full((capacity + extra,), SENTINEL64, dtype=torch.int64, device="cuda")
+    elif flags & vox.OUT_LIST32:
+        list_t = torch.full((capacity + extra,), SENTINEL32, dtype=torch.int32, device="cuda")
+    mask_t = None
+    if flags & vox.OUT_BITMASK:
+        words = vox.vox_mask_words(dims)
+        if mask_init is None:
+            mask_t = torch.zeros(words, dtype=torch.int32, device="cuda")
+        else:
+            mask_t = torch.from_numpy(mask_init.view(np.int32).copy()).cuda()
+    fn = vox.vox_generate_from_scan if use_from_scan else vox.vox_generate
+    fn(segs, dims, ws, status, list_t, mask_t, flags=flags, capacity=capacity)
+    torch.cuda.synchronize()
+    res["status"] = int(status.item())
+    if list_t is not None:
+        res["list_full"] = list_t.cpu().numpy()
+    if mask_t is not None:
+        res["mask"] = mask_t.cpu().numpy().view(np.uint32)
+    return res
+
+
+def oracle_list(O, segs, flags):
+    return O.list64(segs) if flags & vox.OUT_LIST64 else O.list32(segs)
+
+
+def assert_list_equal(got_full, want, V, extra=64):
+    got = got_full[:V]
+    if got.dtype == np.int32:
+        got = got.view(np.uint32)
+    elif got.dtype == np.int64:
+        got = got.view(np.uint64)
+    if not np.array_equal(got, want):
+        bad = np.flatnonzero(got != want)
+        raise AssertionError(f"{len(bad)} list mismatches, first at {bad[:8]}: got {got[bad[:8]]}, want {want[bad[:8]]}")
+    tail = got_full[V:]
+    sentinel = SENTINEL64 if got_full.dtype == np.int64 else SENTINEL32
+    assert (tail == sentinel).all(), "write past the end of the list"
+
+
+def sparse_mask_from_list64(l64: np.ndarray, dims):
+    """Nonzero words of the volume holding the voxels of an oracle 64-bit list:
+    (sorted word indices, OR of their bits)."""
+    w, h, _ = (int(v) for v in dims)
+    m = np.uint64((1 << 21) - 1)
+    x = (l64 & m).astype(np.int64)
+    y = ((l64 >> np.uint64(21)) & m).astype(np.int64)
+    z = ((l64 >> np.uint64(42)) & m).astype(np.int64)
+    lin = x + w * (y + h * z)
+    word = lin >> 5
+    bit = (np.int64(1) << (lin & 31)).astype(np.uint32)
+    order = np.argsort(word, kind="stable")
+    word, bit = word[order], bit[order]
+    starts = np.flatnonzero(np.concatenate([[True], word[1:] != word[:-1]]))
+    return word[starts], np.bitwise_or.reduceat(bit, starts)
+
+
+def check_mask_sparse(mask_t: torch.Tensor, words: np.ndarray, bits: np.ndarray):
+    """The device volume has exactly these nonzero words with these bits."""
+    idx = torch.from_numpy(words).cuda()
+    got = mask_t[idx].cpu().numpy().view(np.uint32)
+    assert np.array_equal(got, bits), f"{int((got != bits).sum())} volume words differ"
+    nnz = int(torch.count_nonzero(mask_t).item())
+    assert nnz == len(words), f"{nnz} nonzero words on the device, {len(words)} expected"
+
+
+def get_oracle():
+    return oracle.get()

@@ -1,0 +1,304 @@
+"""CUDA path against the oracle, element by element, through the C ABI.
+
+Bit-exact for every output (lists, volume words, counts, offsets): the method is
+integer-only, so the tolerance is zero. Sizes span several scan tiles (2048
+segments), several generation windows (1024 segments) and ragged tails; the
+full-size workloads run in the launch configuration that bench.py times.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import (assert_list_equal, check_mask_sparse, get_oracle, oracle_list, run_gpu,
+                      sparse_mask_from_list64)
+from paper_2009_09500_gb300 import vox, workloads
+
+pytestmark = pytest.mark.gpu
+
+L32, L64, BM = vox.OUT_LIST32, vox.OUT_LIST64, vox.OUT_BITMASK
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2009_09500_gb300 import build
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build_library()
+    vox.load()
+
+
+def full_check(segs, dims, flags, **kw):
+    O = get_oracle()
+    r = run_gpu(segs, dims, flags, **kw)
+    assert r["count_status"] == 0 and r["status"] == 0, (r["count_status"], r["status"])
+    counts = O.count(segs)
+    off = O.offsets(counts)
+    assert np.array_equal(r["counts"], counts)
+    assert np.array_equal(r["offsets"], off)
+    assert r["V"] == off[-1]
+    if flags & (L32 | L64):
+        assert_list_equal(r["list_full"], oracle_list(O, segs, flags), r["V"])
+    if flags & BM:
+        want = O.bitmask(segs, dims, None if kw.get("mask_init") is None else kw["mask_init"].copy())
+        assert np.array_equal(r["mask"], want), f"{int((r['mask'] != want).sum())} volume words differ"
+    return r
+
+
+# ------------------------------------------------------------ paper-shaped workloads
+def test_config1_list32_and_mask():
+    w = workloads.config1()
+    full_check(w.segs, w.dims, L32 | BM)
+
+
+def test_config1_each_output_alone():
+    w = workloads.config1()
+    for flags in (L32, L64, BM, L64 | BM):
+        full_check(w.segs, w.dims, flags)
+
+
+def test_config2_full_size_list32_and_mask():
+    """1M fixed 64-voxel segments + one 1023-step segment, 1024^3 volume: the
+    benchmarked workload, whole outputs compared."""
+    w = workloads.config2()
+    full_check(w.segs, w.dims, L32 | BM)
+
+
+def test_config2_single_long_segment():
+    w = workloads.single_long_segment()
+    full_check(w.segs, w.dims, L32 | BM)
+    full_check(w.segs, w.dims, L64)
+
+
+def test_config3_prefix_list64_and_sparse_mask():
+    """Log-uniform lengths in a 4096^3 volume (8 GiB of bits, beyond 2^32):
+    whole list and every nonzero volume word compared."""
+    w = workloads.config3(n=60000)
+    O = get_oracle()
+    segs = torch.from_numpy(w.segs).cuda()
+    n = segs.shape[0]
+    ws = torch.empty(vox.vox_workspace_size(n), dtype=torch.uint8, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    want = O.list64(w.segs)
+    V = len(want)
+    lst = torch.empty(V, dtype=torch.int64, device="cuda")
+    mask = torch.zeros(vox.vox_mask_words(w.dims), dtype=torch.int32, device="cuda")
+    vox.vox_generate(segs, w.dims, ws, status, lst, mask)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    assert np.array_equal(lst.cpu().numpy().view(np.uint64), want)
+    words, bits = sparse_mask_from_list64(want, w.dims)
+    check_mask_sparse(mask, words, bits)
+
+
+def test_config3_full_size_sampled():
+    """All 4M segments (V ~ 2.07e9 > 2^31) with the 64-bit list (16.5 GB) and the
+    8 GiB volume: counts and offsets compared in full, 3000 sampled segments'
+    voxels compared in the list and found set in the volume."""
+    w = workloads.config3()
+    O = get_oracle()
+    segs = torch.from_numpy(w.segs).cuda()
+    n = segs.shape[0]
+    ws = torch.empty(vox.vox_workspace_size(n), dtype=torch.uint8, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    counts = O.count(w.segs)
+    off = O.offsets(counts)
+    V = int(off[-1])
+    assert V > (1 << 31)
+    d_off = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    vox.vox_count(segs, w.dims, ws, status, None, d_off)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    assert np.array_equal(d_off.cpu().numpy(), off)
+    lst = torch.empty(V, dtype=torch.int64, device="cuda")
+    mask = torch.zeros(vox.vox_mask_words(w.dims), dtype=torch.int32, device="cuda")
+    vox.vox_generate(segs, w.dims, ws, status, lst, mask)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    rng = np.random.default_rng(99)
+    sample = np.unique(np.concatenate([rng.integers(0, n, size=3000), [0, n - 1]]))
+    wdim, hdim = w.dims[0], w.dims[1]
+    for chunk in np.array_split(sample, 10):
+        idx = np.concatenate([np.arange(off[s], off[s + 1]) for s in chunk])
+        got = lst[torch.from_numpy(idx).cuda()].cpu().numpy().view(np.uint64)
+        want = np.concatenate([O.list64(w.segs[s:s + 1]) for s in chunk])
+        assert np.array_equal(got, want)
+        words, bits = sparse_mask_from_list64(want, w.dims)
+        m = mask[torch.from_numpy(words).cuda()].cpu().numpy().view(np.uint32)
+        assert ((m & bits) == bits).all(), "a sampled voxel is missing from the volume"
+    del lst, mask
+    torch.cuda.empty_cache()
+
+
+# --------------------------------------------------------------------- edge cases
+def test_empty_input():
+    r = run_gpu(np.zeros((0, 6), np.int32), (8, 8, 8), L32 | BM)
+    assert r["status"] == 0 and r["V"] == 0
+    assert (r["mask"] == 0).all()
+
+
+def test_degenerate_segments_back_to_back():
+    """5000 one-voxel segments: more segments than a staged window holds."""
+    rng = np.random.default_rng(1)
+    p = rng.integers(0, 32, size=(5000, 3)).astype(np.int32)
+    segs = np.concatenate([p, p], axis=1)
+    full_check(segs, (32, 32, 32), L32 | BM)
+    full_check(segs, (32, 32, 32), L64)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 1023, 1024, 1025, 2047, 2048, 2049, 4097, 6143, 10001])
+def test_ragged_sizes(n):
+    rng = np.random.default_rng(n)
+    segs = workloads.uniform_segments(rng, n, (64, 48, 40))
+    full_check(segs, (64, 48, 40), L32 | BM)
+
+
+def test_mixed_lengths_and_windows():
+    """Short and long segments interleaved so that windows end mid-run and runs
+    cross many segment boundaries."""
+    rng = np.random.default_rng(5)
+    parts = []
+    for _ in range(40):
+        k = int(rng.integers(1, 3000))
+        L = int(rng.choice([0, 1, 2, 3, 7, 64, 500, 1023]))
+        parts.append(workloads._segments_from_major(rng, np.full(k, L, np.int64), 1024))
+    segs = np.ascontiguousarray(np.concatenate(parts))
+    full_check(segs, (1024, 1024, 1024), L32 | BM)
+
+
+def test_ties_and_directions():
+    segs = []
+    for N in (2, 4, 6, 10, 64, 1000):
+        m = N // 2
+        for sx in (1, -1):
+            for sy in (1, -1):
+                for sz in (1, -1):
+                    S = np.array([N if sx < 0 else 0, m if sy < 0 else 0, m if sz < 0 else 0])
+                    E = S + np.array([sx * N, sy * m, sz * m])
+                    segs.append(np.concatenate([S, E]))
+                    segs.append(np.concatenate([E, S]))
+                    segs.append(np.concatenate([S[[1, 0, 2]], E[[1, 0, 2]]]))
+                    segs.append(np.concatenate([S[[2, 1, 0]], E[[2, 1, 0]]]))
+    full_check(np.array(segs, dtype=np.int32), (1024, 1024, 1024), L32 | BM)
+
+
+def test_long_segments_wide_division():
+    """N above 46340 takes the 64-bit division when a run enters mid-segment."""
+    rng = np.random.default_rng(8)
+    edge = 1 << 21
+    dims = (edge, 16, 8)
+    segs = []
+    for _ in range(6):
+        x0, x1 = (0, edge - 1) if rng.random() < 0.5 else (edge - 1, 0)
+        segs.append([x0, int(rng.integers(0, 16)), int(rng.integers(0, 8)), x1, int(rng.integers(0, 16)),
+                     int(rng.integers(0, 8))])
+    segs.append([5, 0, 0, 5 + 70001, 15, 7])
+    segs = np.array(segs, dtype=np.int32)
+    full_check(segs, dims, L64 | BM)
+
+
+def test_volume_not_word_aligned():
+    rng = np.random.default_rng(6)
+    dims = (13, 7, 5)
+    segs = workloads.uniform_segments(rng, 3000, dims)
+    full_check(segs, dims, L32 | BM)
+
+
+def test_mask_is_ored_into():
+    rng = np.random.default_rng(7)
+    dims = (64, 64, 64)
+    segs = workloads.uniform_segments(rng, 500, dims)
+    init = rng.integers(0, 2**32, size=vox.vox_mask_words(dims), dtype=np.uint64).astype(np.uint32)
+    init[::3] = 0
+    full_check(segs, dims, BM, mask_init=init)
+
+
+def test_from_scan_matches():
+    w = workloads.config1()
+    full_check(w.segs, w.dims, L32 | BM, use_from_scan=True)
+
+
+def test_capacity_exact_and_too_small():
+    w = workloads.config1()
+    O = get_oracle()
+    V = O.total(w.segs)
+    full_check(w.segs, w.dims, L32, capacity=V)
+    r = run_gpu(w.segs, w.dims, L32 | BM, capacity=V - 1)
+    assert r["status"] == vox.ERR_CAPACITY
+    assert (r["list_full"] == -0x21524111).all(), "nothing may be written on a capacity error"
+    assert (r["mask"] == 0).all()
+
+
+def test_out_of_bounds_endpoint_writes_nothing():
+    w = workloads.config1()
+    segs = w.segs.copy()
+    segs[1234, 4] = 256  # y1 outside [0, 256)
+    r = run_gpu(segs, w.dims, L32 | BM)
+    assert r["count_status"] == vox.ERR_OUT_OF_BOUNDS and r["status"] == vox.ERR_OUT_OF_BOUNDS
+    assert (r["list_full"] == -0x21524111).all()
+    assert (r["mask"] == 0).all()
+    segs = w.segs.copy()
+    segs[7, 0] = -1
+    r = run_gpu(segs, w.dims, L32)
+    assert r["status"] == vox.ERR_OUT_OF_BOUNDS
+
+
+def test_host_side_errors_launch_nothing():
+    segs = torch.zeros((4, 6), dtype=torch.int32, device="cuda")
+    ws = torch.empty(vox.vox_workspace_size(4), dtype=torch.uint8, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    lst = torch.empty(16, dtype=torch.int32, device="cuda")
+    with pytest.raises(vox.VoxError) as e:
+        vox.vox_generate(segs, (2048, 8, 8), ws, st, lst)
+    assert e.value.status == vox.ERR_PACK_WIDTH
+    with pytest.raises(vox.VoxError) as e:
+        vox.vox_generate(segs, (0, 8, 8), ws, st, lst)
+    assert e.value.status == vox.ERR_INVALID_ARG
+    with pytest.raises(vox.VoxError) as e:
+        vox.vox_generate(segs, (8, 8, 8), ws[:64], st, lst)
+    assert e.value.status == vox.ERR_WORKSPACE
+    big = torch.zeros((5, 6), dtype=torch.int32, device="cuda")
+    with pytest.raises(vox.VoxError) as e:
+        vox.vox_generate(big[1:], (8, 8, 8), ws, st, lst)  # 24-byte offset: not 16-byte aligned
+    assert e.value.status == vox.ERR_ALIGNMENT
+
+
+def test_scan_wait_is_bounded():
+    """Fault injection on the host side of the GPU: one scan tile withholds its
+    prefix; the look-back of the next tile gives up after 50 ms and reports
+    VOX_ERR_TIMEOUT; the context stays usable and the next call is correct."""
+    rng = np.random.default_rng(9)
+    dims = (64, 64, 64)
+    segs = workloads.uniform_segments(rng, 3 * vox.vox_scan_tile_segments() + 17, dims)
+    try:
+        vox.vox_debug_set_scan_stall(1, 50_000_000)
+        r = run_gpu(segs, dims, L32 | BM)
+        assert r["count_status"] == vox.ERR_TIMEOUT
+        assert r["status"] == vox.ERR_TIMEOUT
+        assert (r["mask"] == 0).all()
+    finally:
+        vox.vox_debug_set_scan_stall(-1, 0)
+    full_check(segs, dims, L32 | BM)
+
+
+def test_generate_host_matches():
+    w = workloads.config1()
+    O = get_oracle()
+    V = O.total(w.segs)
+    h_segs = torch.from_numpy(w.segs).pin_memory()
+    h_list = torch.empty(V, dtype=torch.int32).pin_memory()
+    h_mask = torch.full((vox.vox_mask_words(w.dims),), 7, dtype=torch.int32).pin_memory()
+    flags = L32 | BM
+    arena = torch.empty(vox.vox_host_arena_size(w.n, w.dims, flags, V), dtype=torch.uint8, device="cuda")
+    got_V = vox.vox_generate_host(h_segs, w.dims, arena, h_list, h_mask)
+    assert got_V == V
+    assert np.array_equal(h_list.numpy().view(np.uint32), O.list32(w.segs))
+    assert np.array_equal(h_mask.numpy().view(np.uint32), O.bitmask(w.segs, w.dims))
+
+
+def test_repeated_calls_are_stable():
+    w = workloads.config2(n_fixed=30000)
+    r1 = run_gpu(w.segs, w.dims, L32 | BM)
+    r2 = run_gpu(w.segs, w.dims, L32 | BM)
+    assert np.array_equal(r1["list_full"], r2["list_full"])
+    assert np.array_equal(r1["mask"], r2["mask"])
