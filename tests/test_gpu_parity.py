@@ -92,7 +92,7 @@ def test_config3_prefix_list64_and_sparse_mask():
 
 
 def test_config3_full_size_sampled():
-    """All 4M segments (V ~ 2.07e9 > 2^31) with the 64-bit list (16.5 GB) and the
+    """All 4M segments (V ~ 2.07e9) with the 64-bit list (16.5 GB) and the
     8 GiB volume: counts and offsets compared in full, 3000 sampled segments'
     voxels compared in the list and found set in the volume."""
     w = workloads.config3()
@@ -104,7 +104,7 @@ def test_config3_full_size_sampled():
     counts = O.count(w.segs)
     off = O.offsets(counts)
     V = int(off[-1])
-    assert V > (1 << 31)
+    assert V > 2_000_000_000 and 8 * V > (1 << 34)  # list byte offsets and volume bit indices beyond 32 bits
     d_off = torch.empty(n + 1, dtype=torch.int64, device="cuda")
     vox.vox_count(segs, w.dims, ws, status, None, d_off)
     torch.cuda.synchronize()
@@ -126,6 +126,41 @@ def test_config3_full_size_sampled():
         words, bits = sparse_mask_from_list64(want, w.dims)
         m = mask[torch.from_numpy(words).cuda()].cpu().numpy().view(np.uint32)
         assert ((m & bits) == bits).all(), "a sampled voxel is missing from the volume"
+    del lst, mask
+    torch.cuda.empty_cache()
+
+
+def test_total_beyond_2_to_31_sampled():
+    """1.1M segments of 2000 voxels in the 4096^3 volume: V = 2.2e9 > 2^31, so the
+    scan totals, offsets and voxel ids need 64 bits. Offsets compared in full,
+    sampled segments compared in the 64-bit list and the volume."""
+    rng = np.random.default_rng(31)
+    n = 1_100_000
+    segs = workloads._segments_from_major(rng, np.full(n, 1999, np.int64), 4096)
+    dims = (4096, 4096, 4096)
+    O = get_oracle()
+    off = O.offsets(O.count(segs))
+    V = int(off[-1])
+    assert V == n * 2000 and V > (1 << 31)
+    d_segs = torch.from_numpy(segs).cuda()
+    ws = torch.empty(vox.vox_workspace_size(n), dtype=torch.uint8, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    d_off = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    vox.vox_count(d_segs, dims, ws, status, None, d_off)
+    lst = torch.empty(V, dtype=torch.int64, device="cuda")
+    mask = torch.zeros(vox.vox_mask_words(dims), dtype=torch.int32, device="cuda")
+    vox.vox_generate(d_segs, dims, ws, status, lst, mask)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    assert np.array_equal(d_off.cpu().numpy(), off)
+    sample = np.unique(np.concatenate([rng.integers(0, n, size=400), [0, n // 2, n - 1]]))
+    idx = np.concatenate([np.arange(off[s], off[s + 1]) for s in sample])
+    got = lst[torch.from_numpy(idx).cuda()].cpu().numpy().view(np.uint64)
+    want = np.concatenate([O.list64(segs[s:s + 1]) for s in sample])
+    assert np.array_equal(got, want)
+    words, bits = sparse_mask_from_list64(want, dims)
+    m = mask[torch.from_numpy(words).cuda()].cpu().numpy().view(np.uint32)
+    assert ((m & bits) == bits).all()
     del lst, mask
     torch.cuda.empty_cache()
 
