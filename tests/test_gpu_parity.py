@@ -104,7 +104,7 @@ def test_config3_full_size_sampled():
     counts = O.count(w.segs)
     off = O.offsets(counts)
     V = int(off[-1])
-    assert V > 2_000_000_000 and 8 * V > (1 << 34)  # list byte offsets and volume bit indices beyond 32 bits
+    assert V > 2_000_000_000 and 8 * V > (1 << 33)  # list byte offsets beyond 33 bits
     d_off = torch.empty(n + 1, dtype=torch.int64, device="cuda")
     vox.vox_count(segs, w.dims, ws, status, None, d_off)
     torch.cuda.synchronize()
