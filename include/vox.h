@@ -151,6 +151,42 @@ vox_status vox_generate_host(const vox_segment *h_segs, int64_t n, vox_dims dims
                              void *h_list, int64_t list_capacity, uint32_t *h_mask, int flags,
                              void *d_arena, size_t arena_bytes, int64_t *h_total, void *stream);
 
+/*
+ * vox_generate_noalloc -- vox_generate without a caller-provided workspace.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory at the point where they voxelize, such as
+ * code running while a stream is captured into a CUDA graph in global capture
+ * mode (where cudaMalloc is not allowed), plug-ins inside a host application
+ * that owns the whole device-memory budget through its own pool, or real-time
+ * loops that cannot pay for cudaMalloc/cudaFree (cudaFree synchronises the
+ * device). The caller still provides the segments, the outputs and the status
+ * word, exactly as for vox_generate (same arguments, same results).
+ *
+ * Scratch: the count/scan scratch lives in a static device array inside the
+ * library, VOX_NOALLOC_SCRATCH_BYTES bytes (about 15.3 MiB), which every GPU
+ * that loads the library holds until the process exits. It is sized for at
+ * most VOX_NOALLOC_MAX_SEGMENTS segments per call; a larger n returns
+ * VOX_ERR_WORKSPACE at once and launches nothing. The call allocates nothing
+ * (no cudaMalloc, cudaFree or allocating library routine).
+ *
+ * Set-up: the first call on each device looks up the device address of the
+ * array with cudaGetSymbolAddress, with that device current. Make that first
+ * call outside any stream capture (for example once at start-up).
+ *
+ * Sharing: every call on a device uses the same array, which keeps the
+ * contents of the last call. Each call clears, with a stream-ordered memset,
+ * the part that must start at zero (the scan's tile counter and flags) and
+ * overwrites the rest. Calls whose work overlaps on the GPU (issued on
+ * different streams, or from several host threads without ordering) race on
+ * the array and can corrupt each other's results: issue them on one stream or
+ * order them with events.
+ */
+#define VOX_NOALLOC_MAX_SEGMENTS 2000000
+#define VOX_NOALLOC_SCRATCH_BYTES 16008448
+vox_status vox_generate_noalloc(const vox_segment *d_segs, int64_t n, vox_dims dims,
+                                void *d_list, int64_t list_capacity, uint32_t *d_mask, int flags,
+                                int32_t *d_status, void *stream);
+
 /* Human-readable name of a status code. Never NULL. */
 const char *vox_strerror(int status);
 

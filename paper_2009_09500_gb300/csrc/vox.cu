@@ -180,9 +180,53 @@ vox_status launch_generate(const vox_segment *segs, int64_t n, vox_dims dims, vo
     return lin64 ? launch_gen_t<kOutMask, true>(p, stream) : launch_gen_t<kOutMask, false>(p, stream);
 }
 
+// ---- allocation-free variant: scratch in a static device array -------------
+// Same layout as ws_layout(VOX_NOALLOC_MAX_SEGMENTS): ticket region, tile
+// descriptors, offsets; each region rounded up to 256 bytes.
+constexpr int64_t kNoAllocMaxSegments = VOX_NOALLOC_MAX_SEGMENTS;
+constexpr size_t round256(size_t x) { return (x + 255) / 256 * 256; }
+constexpr size_t kNoAllocScratchBytes =
+    256 + round256(8 * static_cast<size_t>((kNoAllocMaxSegments + kScanTile - 1) / kScanTile)) +
+    round256(8 * static_cast<size_t>(kNoAllocMaxSegments + 4));
+static_assert(kNoAllocScratchBytes == VOX_NOALLOC_SCRATCH_BYTES, "scratch size in vox.h is stale");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of the static scratch on the current device, looked up once
+// per device (host code must not use the symbol itself as a device pointer).
+vox_status noalloc_scratch(void **out)
+{
+    static std::mutex mu;
+    static std::map<int, void *> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return VOX_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(dev);
+    if (it != cache.end()) {
+        *out = it->second;
+        return VOX_OK;
+    }
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr) return VOX_ERR_CUDA;
+    cache[dev] = ptr;
+    *out = ptr;
+    return VOX_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+vox_status vox_generate_noalloc(const vox_segment *d_segs, int64_t n, vox_dims dims, void *d_list,
+                                int64_t list_capacity, uint32_t *d_mask, int flags, int32_t *d_status, void *stream)
+{
+    if (n > kNoAllocMaxSegments) return VOX_ERR_WORKSPACE;
+    if (n >= 0 && ws_layout(n).total > kNoAllocScratchBytes) return VOX_ERR_WORKSPACE;
+    void *scratch = nullptr;
+    if (vox_status e = noalloc_scratch(&scratch)) return e;
+    return vox_generate(d_segs, n, dims, d_list, list_capacity, d_mask, flags, scratch, kNoAllocScratchBytes,
+                        d_status, stream);
+}
 
 size_t vox_workspace_size(int64_t n_segments)
 {

@@ -36,8 +36,9 @@ OUT_BITMASK = 4
 EXPORTED = (
     "vox_workspace_size", "vox_count", "vox_generate", "vox_generate_from_scan",
     "vox_host_arena_size", "vox_generate_host", "vox_strerror", "vox_mask_words",
-    "vox_debug_set_scan_stall", "vox_scan_tile_segments",
+    "vox_debug_set_scan_stall", "vox_scan_tile_segments", "vox_generate_noalloc",
 )
+NOALLOC_MAX_SEGMENTS = 2000000
 
 
 class Dims(ctypes.Structure):
@@ -91,6 +92,8 @@ def load(path: str | None = None):
     lib.vox_debug_set_scan_stall.restype = None
     lib.vox_scan_tile_segments.argtypes = []
     lib.vox_scan_tile_segments.restype = i64
+    lib.vox_generate_noalloc.argtypes = [vp, i64, Dims, vp, i64, vp, i32, vp, vp]
+    lib.vox_generate_noalloc.restype = i32
     if path == _build.LIB:
         _lib = lib
     return lib
@@ -189,6 +192,25 @@ def vox_generate_from_scan(segs, dims, ws, status, list_out=None, mask=None, fla
                            capacity=None):
     st = _gen(load().vox_generate_from_scan, segs, dims, ws, status, list_out, mask, flags, stream, capacity)
     _check(st, "vox_generate_from_scan")
+
+
+def vox_generate_noalloc(segs, dims, status, list_out=None, mask=None, flags=None, stream=None, capacity=None):
+    """vox_generate for callers that cannot allocate device memory: the scratch
+    is the library's static device array (at most NOALLOC_MAX_SEGMENTS segments
+    per call). Calls that overlap on the GPU share that array and race."""
+    import torch
+
+    _check_segs(segs)
+    if flags is None:
+        flags = 0
+        if list_out is not None:
+            flags |= OUT_LIST64 if list_out.dtype in (torch.int64, torch.uint64) else OUT_LIST32
+        if mask is not None:
+            flags |= OUT_BITMASK
+    cap = int(capacity if capacity is not None else (list_out.numel() if list_out is not None else 0))
+    st = load().vox_generate_noalloc(_ptr(segs), segs.shape[0], _dims(dims), _ptr(list_out), cap, _ptr(mask),
+                                     int(flags), _ptr(status), _stream(stream))
+    _check(st, "vox_generate_noalloc")
 
 
 def vox_host_arena_size(n: int, dims, flags: int, capacity: int) -> int:
