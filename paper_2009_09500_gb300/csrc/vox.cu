@@ -20,7 +20,6 @@ using namespace vox;
 
 constexpr size_t kWsAlign = 256;
 constexpr int64_t kMaxDim = int64_t(1) << 21;
-constexpr int kRun = 16;                      // voxels per thread run in k_generate
 constexpr int64_t kMinPerCta = 2048;          // smallest voxel range given to one CTA
 constexpr int64_t kDefaultWaitNs = 500000000;  // 0.5 s bound on every in-kernel wait
 
@@ -91,6 +90,24 @@ int blocks_per_sm(const void *kernel, int threads, size_t smem)
     return b;
 }
 
+// Opt a kernel in to `smem` bytes of dynamic shared memory (above the 48 KB
+// default), once per kernel and device.
+vox_status allow_smem(const void *kernel, size_t smem)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, bool> done;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return VOX_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(mu);
+    auto key = std::make_pair(kernel, dev);
+    if (done.count(key)) return VOX_OK;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
+        cudaSuccess)
+        return VOX_ERR_CUDA;
+    done[key] = true;
+    return VOX_OK;
+}
+
 // Host-side checks shared by the generation entry points.
 vox_status check_generate_args(const vox_segment *segs, int64_t n, vox_dims dims, const void *list,
                                int64_t capacity, const uint32_t *mask, int flags, const void *ws,
@@ -140,8 +157,11 @@ vox_status launch_count_scan(const vox_segment *segs, int64_t n, vox_dims dims, 
 template <int OUT, bool LIN64>
 vox_status launch_gen_t(const GenParams &p, cudaStream_t stream)
 {
-    auto kernel = k_generate<kRun, OUT, LIN64>;
-    const size_t smem = sizeof(GenSmem<kRun>);
+    // run length: 32 voxels per thread, 16 when the 64-bit list doubles the staging
+    constexpr int R = (OUT & kOutList64) ? 16 : 32;
+    auto kernel = k_generate<R, OUT, LIN64>;
+    const size_t smem = sizeof(GenSmem<R, OUT>);
+    if (vox_status e = allow_smem(reinterpret_cast<const void *>(kernel), smem)) return e;
     const int per_sm = blocks_per_sm(reinterpret_cast<const void *>(kernel), kGenThreads, smem);
     const int sms = sm_count();
     if (per_sm <= 0 || sms <= 0) return VOX_ERR_CUDA;

@@ -162,16 +162,18 @@ __device__ __forceinline__ T signed_step(int32_t d, T unit)
 
 // Stepping state of one segment. PackT: uint32_t (LIST32) or uint64_t (LIST64);
 // LinT: uint32_t or uint64_t volume bit index (volumes up to or beyond 2^32 bits).
+// The three minor/major roles are fixed at entry: the major axis (|d| = N) moves
+// every step, the two minor axes move when their remainder reaches 2N.
 template <typename PackT, typename LinT>
 struct Stepper {
-    int32_t left;     // steps still to take inside this segment (N - k)
+    int32_t left;     // steps still to take inside this segment after entry (N - k)
     int32_t twoN;     // 2N
     int32_t Ab2, Ac2; // 2|d| of the two minor axes
     int32_t rb, rc;   // their remainders
     PackT P, dPm, dPb, dPc;
     LinT L, dLm, dLb, dLc;
 
-    // Enter segment (x0, y0, z0) -> (x1, y1, z1) at step k.
+    // Enter segment (x0, y0, z0) -> (x1, y1, z1) at step k (0 <= k <= N).
     __device__ __forceinline__ void enter(const int32_t *rec, int32_t k, LinT w, LinT wh)
     {
         const int32_t x0 = rec[0], y0 = rec[1], z0 = rec[2];
@@ -181,7 +183,7 @@ struct Stepper {
         left = N - k;
         twoN = 2 * N;
         int32_t qx = 0, qy = 0, qz = 0, rx = N, ry = N, rz = N;
-        if (N > 0) {
+        if (k > 0) {  // k = 0: every offset is 0 and every remainder N
             axis_entry(ax, N, k, qx, rx);
             axis_entry(ay, N, k, qy, ry);
             axis_entry(az, N, k, qz, rz);
@@ -216,23 +218,24 @@ struct Stepper {
         dLc = signed_step<LinT>(dc, uc);
     }
 
-    // One step along the segment (requires left > 0).
+    // One step along the segment. Stepping past the last voxel is harmless (the
+    // state is simply not used again), so callers may step once too often.
+    template <bool kP, bool kL>
     __device__ __forceinline__ void step()
     {
-        --left;
-        P += dPm;
-        L += dLm;
+        if (kP) P += dPm;
+        if (kL) L += dLm;
         rb += Ab2;
         if (rb >= twoN) {
             rb -= twoN;
-            P += dPb;
-            L += dLb;
+            if (kP) P += dPb;
+            if (kL) L += dLb;
         }
         rc += Ac2;
         if (rc >= twoN) {
             rc -= twoN;
-            P += dPc;
-            L += dLc;
+            if (kP) P += dPc;
+            if (kL) L += dLc;
         }
     }
 };

@@ -16,6 +16,7 @@
 // same number of voxels whatever the length mix.
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 #include <type_traits>
 
@@ -34,7 +35,7 @@ constexpr uint64_t kDescInc = 2ull << 62;  // tile inclusive prefix published
 constexpr uint64_t kDescValue = (1ull << 62) - 1;
 
 constexpr int kGenThreads = 256;
-constexpr int kWindowSegs = 1024;  // segment records staged per window (even)
+constexpr int kWindowSegs = 512;   // segment records staged per window (even)
 
 // Status codes written by the kernels (same values as the public vox_status).
 constexpr int32_t kStOutOfBounds = 2;
@@ -221,14 +222,40 @@ struct GenParams {
     int64_t min_per_cta;     // smallest voxel range worth a CTA (multiple of 4)
 };
 
-template <int R>
+// Shared memory of k_generate: the staged window of segments and, for list
+// outputs, the pass's voxels in a transposed layout (run slot u of thread t at
+// u * S + t, S = 256 + 32 / R) that is free of bank conflicts both when the
+// threads write their runs and when the pass is read back four voxels per thread.
+template <int R, int OUT>
+struct GenLayout {
+    static constexpr bool kList = (OUT & (kOutList32 | kOutList64)) != 0;
+    static constexpr bool kWide = (OUT & kOutList64) != 0;
+    static constexpr int S = kGenThreads + 32 / R;
+    static constexpr int kPlanes = kWide ? 2 : 1;
+    static constexpr int kStageWords = kList ? kPlanes * R * S : 4;
+};
+
+// The two TMA destinations (offs, recs) must start on 16-byte boundaries; they
+// lead the struct and their sizes are multiples of 16 (checked below).
+template <int R, int OUT>
 struct GenSmem {
+    alignas(16) int64_t offs[kWindowSegs + 2];
+    alignas(16) int32_t recs[kWindowSegs * 6];
+    alignas(16) uint32_t stage[GenLayout<R, OUT>::kStageWords];
     uint64_t bar;
     int64_t V;
-    int64_t offs[kWindowSegs + 2];
-    int32_t recs[kWindowSegs * 6];
     int32_t go;
+    int32_t pad;
 };
+static_assert((kWindowSegs + 2) * sizeof(int64_t) % 16 == 0, "offs size");
+static_assert(kWindowSegs * 6 * sizeof(int32_t) % 16 == 0, "recs size");
+using GenSmemL32 = GenSmem<32, 1>;
+using GenSmemL64M = GenSmem<16, 6>;
+using GenSmemM = GenSmem<32, 4>;
+static_assert(offsetof(GenSmemL32, offs) % 16 == 0 && offsetof(GenSmemL32, recs) % 16 == 0 &&
+                  offsetof(GenSmemL64M, recs) % 16 == 0 && offsetof(GenSmemM, recs) % 16 == 0 &&
+                  offsetof(GenSmemL32, bar) % 8 == 0,
+              "TMA destinations must be 16-byte aligned");
 
 // Largest s in [lo, hi) with offsets[s] <= g, given offsets[lo] <= g < offsets[hi]:
 // a 256-ary search where each round every thread probes one position. Must be
@@ -261,18 +288,28 @@ __device__ __forceinline__ int32_t find_in_window(const int64_t *offs, int32_t c
     return lo;
 }
 
+// OR `bits` into a volume word as a reduction (no return value), asking L2 to
+// keep the line (the volume is re-touched; list lines are not).
+__device__ __forceinline__ void red_or_keep(uint32_t *addr, uint32_t bits, uint64_t policy)
+{
+    asm volatile("red.relaxed.gpu.global.or.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(addr), "r"(bits), "l"(policy)
+                 : "memory");
+}
+
 template <int R, int OUT, bool LIN64>
 __global__ void __launch_bounds__(kGenThreads) k_generate(GenParams p)
 {
-    using PackT = typename std::conditional<(OUT & kOutList64) != 0, uint64_t, uint32_t>::type;
+    using L = GenLayout<R, OUT>;
+    using PackT = typename std::conditional<L::kWide, uint64_t, uint32_t>::type;
     using LinT = typename std::conditional<LIN64, uint64_t, uint32_t>::type;
-    constexpr bool kList = (OUT & (kOutList32 | kOutList64)) != 0;
+    constexpr bool kList = L::kList;
     constexpr bool kMask = (OUT & kOutMask) != 0;
     constexpr int kPass = kGenThreads * R;
-    static_assert(R % 4 == 0, "runs must keep 16-byte store alignment");
+    constexpr int S = L::S;
+    static_assert(R % 4 == 0 && 32 % R == 0 || R == 32 || R == 64, "run length");
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    GenSmem<R> &sm = *reinterpret_cast<GenSmem<R> *>(smem_raw);
+    GenSmem<R, OUT> &sm = *reinterpret_cast<GenSmem<R, OUT> *>(smem_raw);
     const int t = threadIdx.x;
 
     // prologue decided by one thread so that the whole CTA agrees
@@ -297,21 +334,24 @@ __global__ void __launch_bounds__(kGenThreads) k_generate(GenParams p)
     per = (per + 3) & ~int64_t(3);
     const int64_t gA = static_cast<int64_t>(blockIdx.x) * per;
     if (gA >= V) return;
-    const int64_t gB = min(gA + per, V);
+    const int64_t gB = min64(gA + per, V);
 
+    uint64_t keep_policy = 0;
+    if (kMask) asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep_policy));
     uint32_t phase = 0;
     int64_t s_cur = find_segment_block(p.offsets, 0, p.n, gA);
 
     const LinT w = static_cast<LinT>(p.w);
     const LinT wh = static_cast<LinT>(p.w) * static_cast<LinT>(p.h);
+    PackT *const list = static_cast<PackT *>(p.list);
     int64_t g0 = gA;
     while (g0 < gB) {
         // ---- stage a window of segment records and offsets (TMA bulk copies)
         const int64_t s_base = s_cur & ~int64_t(1);
         const int32_t cnt = static_cast<int32_t>(min64(kWindowSegs, p.n - s_base));
-        const int32_t cnt_bulk = cnt & ~1;             // 24 * even bytes is a multiple of 16
-        const int32_t off_entries = (cnt + 3) & ~1;    // entries s_base .. s_base+cnt (+1 pad), even
-        __syncthreads();  // previous window fully consumed
+        const int32_t cnt_bulk = cnt & ~1;           // 24 * even bytes is a multiple of 16
+        const int32_t off_entries = (cnt + 3) & ~1;  // entries s_base .. s_base+cnt (+1 pad), even
+        __syncthreads();                             // previous window fully consumed
         if (t == 0) {
             fence_proxy_async_smem();
             const uint32_t rec_bytes = static_cast<uint32_t>(cnt_bulk) * 24u;
@@ -326,7 +366,7 @@ __global__ void __launch_bounds__(kGenThreads) k_generate(GenParams p)
         if (__syncthreads_or(!landed)) {
             // a copy did not land in time: report, give it one more bounded wait, stop
             if (t == 0) set_status(p.status, kStTimeout);
-            if (landed == false) mbar_wait_bounded(&sm.bar, phase ^ 1u, p.wait_ns);
+            if (!landed) mbar_wait_bounded(&sm.bar, phase ^ 1u, p.wait_ns);
             return;
         }
 
@@ -334,7 +374,8 @@ __global__ void __launch_bounds__(kGenThreads) k_generate(GenParams p)
         int64_t g_end = gB;
         if (win_end < gB) g_end = win_end & ~int64_t(3);
 
-        // ---- passes over [g0, g_end), R consecutive voxels per thread
+        // ---- passes over [g0, g_end): thread t takes the R consecutive voxels
+        // starting at gp + t R, walking segment by segment
         for (int64_t gp = g0; gp < g_end; gp += kPass) {
             const int64_t g = gp + static_cast<int64_t>(t) * R;
             if (g < g_end) {
@@ -342,61 +383,71 @@ __global__ void __launch_bounds__(kGenThreads) k_generate(GenParams p)
                 int32_t j = find_in_window(sm.offs, cnt, g);
                 Stepper<PackT, LinT> st;
                 st.enter(sm.recs + 6 * j, static_cast<int32_t>(g - sm.offs[j]), w, wh);
-                PackT out[R];
+                uint32_t *sp = sm.stage + t;
                 LinT cur_word = static_cast<LinT>(~LinT(0));
                 uint32_t acc = 0;
-#pragma unroll
-                for (int u = 0; u < R; ++u) {
-                    if (u < len) {
-                        if (kList) out[u] = st.P;
+                int32_t u = 0;
+                while (true) {
+                    const int32_t m = min(st.left + 1, len - u);  // voxels taken from this segment
+#pragma unroll 2
+                    for (int32_t e = 0; e < m; ++e) {
+                        if (kList) {
+                            sp[0] = static_cast<uint32_t>(st.P);
+                            if (L::kWide) sp[R * S] = static_cast<uint32_t>(static_cast<uint64_t>(st.P) >> 32);
+                            sp += S;
+                        }
                         if (kMask) {
                             const LinT word = st.L >> 5;
-                            const uint32_t bit = 1u << (static_cast<uint32_t>(st.L) & 31u);
-                            if (word == cur_word) {
-                                acc |= bit;
-                            } else {
-                                if (acc) atomicOr(p.mask + cur_word, acc);
+                            if (word != cur_word) {
+                                if (acc) red_or_keep(p.mask + cur_word, acc, keep_policy);
                                 cur_word = word;
-                                acc = bit;
+                                acc = 0;
                             }
+                            acc |= 1u << (static_cast<uint32_t>(st.L) & 31u);
                         }
-                        if (u + 1 < len) {
-                            if (st.left == 0) {
-                                ++j;
-                                st.enter(sm.recs + 6 * j, 0, w, wh);
-                            } else {
-                                st.step();
-                            }
-                        }
+                        st.template step<kList, kMask>();
                     }
+                    u += m;
+                    if (u >= len) break;
+                    ++j;  // the run continues in the next segment of the window
+                    st.enter(sm.recs + 6 * j, 0, w, wh);
                 }
-                if (kMask && acc) atomicOr(p.mask + cur_word, acc);
-                if (kList) {
-                    PackT *dst = static_cast<PackT *>(p.list) + g;
-                    if (len == R) {
-                        constexpr int kPerVec = 16 / sizeof(PackT);
+                if (kMask && acc) red_or_keep(p.mask + cur_word, acc, keep_policy);
+            }
+            if (kList) {
+                // ---- write the pass out: four consecutive voxels per thread, 16-byte stores
+                __syncthreads();
+                const int32_t pass_len = static_cast<int32_t>(min64(kPass, g_end - gp));
+                const int32_t n4 = pass_len >> 2;
+                for (int32_t q = t; q < n4; q += kGenThreads) {
+                    const int32_t p0 = 4 * q;
+                    uint32_t lo[4], hi[4];
 #pragma unroll
-                        for (int u = 0; u < R; u += kPerVec) {
-                            if constexpr (sizeof(PackT) == 4) {
-                                uint4 q;
-                                q.x = static_cast<uint32_t>(out[u]);
-                                q.y = static_cast<uint32_t>(out[u + 1]);
-                                q.z = static_cast<uint32_t>(out[u + 2]);
-                                q.w = static_cast<uint32_t>(out[u + 3]);
-                                *reinterpret_cast<uint4 *>(dst + u) = q;
-                            } else {
-                                ulonglong2 q;
-                                q.x = static_cast<unsigned long long>(out[u]);
-                                q.y = static_cast<unsigned long long>(out[u + 1]);
-                                *reinterpret_cast<ulonglong2 *>(dst + u) = q;
-                            }
-                        }
+                    for (int e = 0; e < 4; ++e) {
+                        const int32_t pe = p0 + e;
+                        const int32_t idx = (pe % R) * S + pe / R;
+                        lo[e] = sm.stage[idx];
+                        if (L::kWide) hi[e] = sm.stage[R * S + idx];
+                    }
+                    if constexpr (L::kWide) {
+                        ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(list + gp + p0);
+                        dst[0] = make_ulonglong2(lo[0] | (static_cast<unsigned long long>(hi[0]) << 32),
+                                                 lo[1] | (static_cast<unsigned long long>(hi[1]) << 32));
+                        dst[1] = make_ulonglong2(lo[2] | (static_cast<unsigned long long>(hi[2]) << 32),
+                                                 lo[3] | (static_cast<unsigned long long>(hi[3]) << 32));
                     } else {
-#pragma unroll
-                        for (int u = 0; u < R; ++u)
-                            if (u < len) dst[u] = out[u];
+                        *reinterpret_cast<uint4 *>(list + gp + p0) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
                     }
                 }
+                if (t == 0) {
+                    for (int32_t pe = 4 * n4; pe < pass_len; ++pe) {
+                        const int32_t idx = (pe % R) * S + pe / R;
+                        uint64_t v = sm.stage[idx];
+                        if (L::kWide) v |= static_cast<uint64_t>(sm.stage[R * S + idx]) << 32;
+                        list[gp + pe] = static_cast<PackT>(v);
+                    }
+                }
+                __syncthreads();
             }
         }
         g0 = g_end;
