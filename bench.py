@@ -223,28 +223,31 @@ def run_ours(args):
     n = w.n
     stream = torch.cuda.current_stream()
     segs = torch.from_numpy(w.segs).to(dev)
-    ws = torch.empty(vox.vox_workspace_size(n), dtype=torch.uint8, device=dev)
     status = torch.zeros(1, dtype=torch.int32, device=dev)
-    offsets = torch.empty(n + 1, dtype=torch.int64, device=dev)
-    vox.vox_count(segs, w.dims, ws, status, None, offsets)
-    torch.cuda.synchronize()
-    V = int(offsets[-1].item())
-    assert int(status.item()) == 0
+    # plan once (synchronous): total voxels V and brick pieces P size the list and workspace
+    ws = torch.empty(vox.vox_workspace_size_volume(n, w.dims, 0), dtype=torch.uint8, device=dev)
+    V, P = vox.vox_plan(segs, w.dims, ws, status)
+    ws = torch.empty(vox.vox_workspace_size_volume(n, w.dims, P), dtype=torch.uint8, device=dev)
     lst = torch.empty(V, dtype=torch.int32, device=dev)
     words = vox.vox_mask_words(w.dims)
     mask = torch.zeros(words, dtype=torch.int32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     flags = vox.OUT_LIST32 | vox.OUT_BITMASK
 
-    def step(ev0=None, ev1=None, ev2=None):
-        if ev0 is not None:
-            ev0.record(stream)
+    # one step = the launches of vox_generate(list32 | volume), issued as its three
+    # phases so that each phase gets its own events: count + scan, list, volume
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
         vox.vox_count(segs, w.dims, ws, status, None, None, stream)
-        if ev1 is not None:
-            ev1.record(stream)
-        vox.vox_generate_from_scan(segs, w.dims, ws, status, lst, mask, flags, stream)
-        if ev2 is not None:
-            ev2.record(stream)
+        if ev is not None:
+            ev[1].record(stream)
+        vox.vox_generate_from_scan(segs, w.dims, ws, status, lst, None, vox.OUT_LIST32, stream)
+        if ev is not None:
+            ev[2].record(stream)
+        vox.vox_generate_from_scan(segs, w.dims, ws, status, None, mask, vox.OUT_BITMASK, stream)
+        if ev is not None:
+            ev[3].record(stream)
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -253,10 +256,9 @@ def run_ours(args):
     if int(status.item()) != 0:
         raise RuntimeError(f"device status {vox.strerror(int(status.item()))}")
     # bytes the volume read-modify-writes: 64 B per distinct 32-byte sector touched
-    sectors = int((mask.view(-1, 8) != 0).any(dim=1).sum().item()) if words % 8 == 0 else None
+    sectors = int((mask.view(-1, 8) != 0).any(dim=1).sum().item())
 
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    evs = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(4)) for _ in range(args.steps)]
     sampler = ClockSampler(dev.index if dev.index is not None else 0)
     if world > 1:
         torch.distributed.barrier()
@@ -265,7 +267,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     for k in range(args.steps):
         flush.zero_()
-        step(*evs[k])
+        step(evs[k])
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     if world > 1:
@@ -274,9 +276,10 @@ def run_ours(args):
     st = int(status.item())
     if st != 0:
         raise RuntimeError(f"device status {vox.strerror(st)}")
-    step_ms = [a.elapsed_time(c) for a, b, c in evs]
-    scan_ms = [a.elapsed_time(b) for a, b, c in evs]
-    gen_ms = [b.elapsed_time(c) for a, b, c in evs]
+    step_ms = [e[0].elapsed_time(e[3]) for e in evs]
+    scan_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    list_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    vol_ms = [e[2].elapsed_time(e[3]) for e in evs]
     ms_mean = float(np.mean(step_ms))
     if world > 1:
         t = torch.tensor([ms_mean], dtype=torch.float64, device=dev)
@@ -287,16 +290,25 @@ def run_ours(args):
     total_voxels = V * world
     value = total_voxels / (ms_mean_max / 1000.0)
 
-    # roofline of the dominant kernel (generation): algorithmic bytes per launch
+    # rooflines: algorithmic bytes per launch / mean duration from the step's events
     peaks, peak_kind = _measured_peaks()
-    gen_mean = float(np.mean(gen_ms))
-    alg_bytes = 24 * n + 4 * V + (64 * sectors if sectors is not None else 0)
-    achieved = alg_bytes / (gen_mean / 1000.0) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
-                "frac": achieved / float(peaks["hbm_gbs"]), "traffic": _recorded_traffic("k_generate"),
-                "kernel": "k_generate<16, list32|mask>", "peak_kind": f"{peak_kind} HBM copy",
-                "algorithmic_bytes_per_launch": alg_bytes,
-                "bytes_model": "24 B/segment read + 4 B/voxel list + 64 B per distinct 32-B volume sector"}
+    hbm = float(peaks["hbm_gbs"])
+    list_mean, vol_mean = float(np.mean(list_ms)), float(np.mean(vol_ms))
+    list_bytes = 24 * n + 4 * V
+    vol_bytes = 24 * n + 64 * sectors
+    roof_list = {"bound": "hbm", "achieved": list_bytes / list_mean / 1e6, "peak": hbm, "unit": "GB/s",
+                 "frac": list_bytes / list_mean / 1e6 / hbm, "traffic": _recorded_traffic("k_generate"),
+                 "kernel": "k_generate<32, list32> (one launch)", "peak_kind": f"{peak_kind} HBM copy",
+                 "algorithmic_bytes_per_launch": list_bytes, "ms": list_mean,
+                 "bytes_model": "24 B/segment read + 4 B/voxel written"}
+    roof_vol = {"bound": "hbm", "achieved": vol_bytes / vol_mean / 1e6, "peak": hbm, "unit": "GB/s",
+                "frac": vol_bytes / vol_mean / 1e6 / hbm, "traffic": _recorded_traffic("k_brick_volume"),
+                "kernel": "volume phase: k_bin_count + k_scan<false> + k_bin_scatter + k_brick_volume "
+                          "(+ gated atomic fallback, exits at once)",
+                "peak_kind": f"{peak_kind} HBM copy", "algorithmic_bytes_per_launch": vol_bytes, "ms": vol_mean,
+                "bytes_model": "24 B/segment read + 64 B per distinct 32-B volume sector (read + write)",
+                "pieces": P}
+    roofline, roofline_other = (roof_vol, roof_list) if vol_mean >= list_mean else (roof_list, roof_vol)
 
     # end to end through the host-buffer entry point (copies inside the timed region)
     e2e = None
@@ -332,16 +344,19 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_mean_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "segments": n, "voxels_per_gpu": V, "volume": list(w.dims),
-                   "outputs": "list32 + bitmask", "launch": "plain (count+scan, generate) on one stream",
+                   "outputs": "list32 + bitmask", "volume_path": "brick ownership", "pieces": P,
+                   "launch": "plain (count+scan, list, volume) on one stream",
                    "l2": "flushed between steps by a 256 MiB write (outside the step events)",
                    "parallelism": f"replicas x{world} (independent batches)"},
         "segments_per_s": n * world / (ms_mean_max / 1000.0),
         "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
-        "kernels_ms": {"count_scan": float(np.mean(scan_ms)), "generate": gen_mean},
+        "kernels_ms": {"count_scan": float(np.mean(scan_ms)), "list": list_mean, "volume": vol_mean},
         "wall_s_timed_region": wall,
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-        "gpu_launches": 2 * args.steps,
-        "gpu_launches_note": "k_count_scan + k_generate per step (plus 2 memset nodes)",
+        "roofline": roofline, "roofline_other": roofline_other, "cpu_baseline": cpu, "e2e": e2e,
+        "clocks": clocks,
+        "gpu_launches": 7 * args.steps,
+        "gpu_launches_note": "per step: k_scan<true>, k_generate (list), k_bin_count, k_scan<false>, "
+                             "k_bin_scatter, k_brick_volume, k_generate (gated volume fallback; exits at once)",
     }
     print(json.dumps(line), flush=True)
     if world > 1:

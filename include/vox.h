@@ -134,6 +134,40 @@ vox_status vox_generate_from_scan(const vox_segment *d_segs, int64_t n, vox_dims
                                   void *stream);
 
 /*
+ * The occupancy volume can be built two ways; vox_generate picks one from the
+ * workspace it is given:
+ *   - by brick ownership (volumes whose width w is a multiple of 32): the volume
+ *     is cut into bricks of whole words, each segment into pieces that stay in
+ *     one brick, the pieces are sorted by brick, and one CTA per brick ORs its
+ *     voxels in shared memory and merges them into the volume, so that each
+ *     volume sector is read and written once. Needs a workspace of at least
+ *     vox_workspace_size_volume(n, dims, P) bytes with P >= the number of pieces
+ *     (vox_plan reports it). If the pieces turn out not to fit, the same call
+ *     falls back, on the device, to the per-voxel atomic path (same result).
+ *   - by per-voxel atomic ORs of deduplicated words: any volume, any workspace
+ *     of at least vox_workspace_size(n) bytes.
+ * Both give the same bits. With the brick path the volume's words are written
+ * with plain read-modify-writes: calls that write the same volume must not
+ * overlap on the GPU.
+ *
+ * vox_workspace_size_volume -- workspace bytes for n segments in a volume of
+ * `dims` with room for `piece_capacity` pieces (falls back to
+ * vox_workspace_size(n) when the volume cannot use bricks).
+ */
+size_t vox_workspace_size_volume(int64_t n, vox_dims dims, int64_t piece_capacity);
+
+/*
+ * vox_plan -- SYNCHRONOUS sizing helper: runs the count, the scan and the
+ * brick binning count on the device and returns the total voxel count V and
+ * the number of brick pieces (0 when the volume cannot use bricks), so that
+ * the caller can size the list and the workspace of a following vox_generate.
+ *   d_ws   at least vox_workspace_size_volume(n, dims, 0) bytes
+ *   returns VOX_OK or the first error (host or device)
+ */
+vox_status vox_plan(const vox_segment *d_segs, int64_t n, vox_dims dims, void *d_ws, size_t ws_bytes,
+                    int32_t *d_status, int64_t *h_voxels, int64_t *h_pieces, void *stream);
+
+/*
  * vox_generate_host -- vox_generate on host buffers, copies included (the
  * host-device pipeline of Fig. 4: input copy, kernels, result copy back).
  * SYNCHRONOUS: returns once the results are in host memory (it synchronises

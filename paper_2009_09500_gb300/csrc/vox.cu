@@ -12,6 +12,7 @@
 #include <utility>
 
 #include "vox.h"
+#include "vox_bricks.cuh"
 #include "vox_kernels.cuh"
 
 namespace {
@@ -137,6 +138,8 @@ vox_status launch_count_scan(const vox_segment *segs, int64_t n, vox_dims dims, 
     if (cudaMemsetAsync(base, 0, L.offsets, stream) != cudaSuccess) return VOX_ERR_CUDA;
     ScanParams p;
     p.segs = reinterpret_cast<const int32_t *>(segs);
+    p.counts_in = nullptr;
+    p.offsets_copy = nullptr;
     p.n = n;
     p.w = dims.w;
     p.h = dims.h;
@@ -150,7 +153,7 @@ vox_status launch_count_scan(const vox_segment *segs, int64_t n, vox_dims dims, 
     p.n_tiles = L.n_tiles;
     p.stall_tile = g_stall_tile.load();
     p.wait_ns = static_cast<uint64_t>(g_wait_ns.load());
-    k_count_scan<<<static_cast<unsigned>(L.n_tiles), kScanThreads, 0, stream>>>(p);
+    k_scan<true><<<static_cast<unsigned>(L.n_tiles), kScanThreads, 0, stream>>>(p);
     return cudaGetLastError() == cudaSuccess ? VOX_OK : VOX_ERR_CUDA;
 }
 
@@ -170,7 +173,8 @@ vox_status launch_gen_t(const GenParams &p, cudaStream_t stream)
 }
 
 vox_status launch_generate(const vox_segment *segs, int64_t n, vox_dims dims, void *list, int64_t capacity,
-                           uint32_t *mask, int flags, void *ws, int32_t *status, cudaStream_t stream)
+                           uint32_t *mask, int flags, void *ws, int32_t *status, cudaStream_t stream,
+                           const int64_t *gate_total = nullptr, int64_t gate_cap = 0)
 {
     if (n == 0) return VOX_OK;
     const WsLayout L = ws_layout(n);
@@ -187,6 +191,8 @@ vox_status launch_generate(const vox_segment *segs, int64_t n, vox_dims dims, vo
     p.status = status;
     p.wait_ns = static_cast<uint64_t>(g_wait_ns.load());
     p.min_per_cta = kMinPerCta;
+    p.gate_total = gate_total;
+    p.gate_cap = gate_cap;
     const bool lin64 = volume_bits(dims) > (uint64_t(1) << 32);
     const bool bm = flags & VOX_OUT_BITMASK;
     if (flags & VOX_OUT_LIST32) {
@@ -198,6 +204,141 @@ vox_status launch_generate(const vox_segment *segs, int64_t n, vox_dims dims, vo
                      : launch_gen_t<kOutList64 | kOutMask, false>(p, stream);
     }
     return lin64 ? launch_gen_t<kOutMask, true>(p, stream) : launch_gen_t<kOutMask, false>(p, stream);
+}
+
+// ---- the volume by brick ownership ------------------------------------------
+constexpr int64_t kMaxBricks = int64_t(1) << 26;
+
+// Brick shape for a volume whose rows are whole 32-bit words (w % 32 == 0):
+// B0 = min(w, 256) voxels along x (whole words), then B1 x B2 rows (powers of
+// two) so that a brick has at most kBrickWordsMax words.
+bool make_geom(vox_dims dims, BrickGeom *G)
+{
+    if (check_dims(dims) != VOX_OK || dims.w % 32 != 0) return false;
+    G->B[0] = dims.w < 256 ? dims.w : 256;
+    G->bxw = G->B[0] / 32;
+    const int32_t rows = kBrickWordsMax / G->bxw;
+    int32_t p2 = 1;
+    while ((2 * p2) * (2 * p2) <= rows) p2 *= 2;
+    G->B[1] = (2 * p2 * p2 <= rows) ? 2 * p2 : p2;
+    G->B[2] = p2;
+    G->dim[0] = dims.w;
+    G->dim[1] = dims.h;
+    G->dim[2] = dims.d;
+    G->row_words = dims.w / 32;
+    G->words = G->bxw * G->B[1] * G->B[2];
+    int64_t nb = 1;
+    for (int a = 0; a < 3; ++a) {
+        G->nb[a] = (G->dim[a] + G->B[a] - 1) / G->B[a];
+        nb *= G->nb[a];
+    }
+    G->n_bricks = nb;
+    return nb <= kMaxBricks && G->words <= kBrickWordsMax;
+}
+
+struct VolLayout {
+    int64_t n_tiles;  // scan tiles over the brick counts
+    size_t hdr;       // scan ticket at +0, brick ticket at +128
+    size_t count;     // int32 [n_bricks]
+    size_t desc;      // uint64 [n_tiles]
+    size_t off;       // int64 [n_bricks + 4]
+    size_t cursor;    // int64 [n_bricks + 1]
+    size_t pieces;    // uint64 [capacity]
+    size_t total;
+};
+
+// The volume path's workspace follows the base layout of ws_layout(n).
+VolLayout vol_layout(int64_t n, const BrickGeom &G, int64_t capacity)
+{
+    VolLayout L;
+    const size_t nb = static_cast<size_t>(G.n_bricks);
+    L.n_tiles = (G.n_bricks + kScanTile - 1) / kScanTile;
+    L.hdr = ws_layout(n).total;
+    L.count = L.hdr + kWsAlign;
+    L.desc = L.count + align_up(4 * nb);
+    L.off = L.desc + align_up(8 * static_cast<size_t>(L.n_tiles));
+    L.cursor = L.off + align_up(8 * (nb + 4));
+    L.pieces = L.cursor + align_up(8 * (nb + 1));
+    L.total = L.pieces + align_up(8 * static_cast<size_t>(capacity));
+    return L;
+}
+
+// bin -> scan -> scatter -> per-brick volume, then the atomic kernel, which only
+// runs if the pieces did not fit in the workspace
+vox_status launch_bricks(const vox_segment *segs, int64_t n, const BrickGeom &G, vox_dims dims, uint32_t *mask,
+                         void *ws, size_t ws_bytes, int32_t *status, cudaStream_t stream, bool count_only = false)
+{
+    const VolLayout VL = vol_layout(n, G, 0);
+    const int64_t capacity = static_cast<int64_t>((ws_bytes - VL.pieces) / 8);
+    char *base = static_cast<char *>(ws);
+    if (cudaMemsetAsync(base + VL.hdr, 0, VL.off - VL.hdr, stream) != cudaSuccess) return VOX_ERR_CUDA;
+    BinParams bp;
+    bp.segs = reinterpret_cast<const int32_t *>(segs);
+    bp.n = n;
+    bp.G = G;
+    bp.brick_count = reinterpret_cast<int32_t *>(base + VL.count);
+    bp.cursor = reinterpret_cast<int64_t *>(base + VL.cursor);
+    bp.brick_off = reinterpret_cast<const int64_t *>(base + VL.off);
+    bp.pieces = reinterpret_cast<uint64_t *>(base + VL.pieces);
+    bp.capacity = capacity;
+    bp.status = status;
+    const int sms = sm_count();
+    if (sms <= 0) return VOX_ERR_CUDA;
+    int64_t bin_blocks = (n + 255) / 256;
+    if (bin_blocks > 8 * sms) bin_blocks = 8 * sms;
+    k_bin_count<<<static_cast<unsigned>(bin_blocks), 256, 0, stream>>>(bp);
+    ScanParams sp;
+    sp.segs = nullptr;
+    sp.counts_in = bp.brick_count;
+    sp.offsets_copy = bp.cursor;
+    sp.n = G.n_bricks;
+    sp.w = sp.h = sp.d = 0;
+    sp.counts = nullptr;
+    sp.offsets = reinterpret_cast<int64_t *>(base + VL.off);
+    sp.offsets_out = nullptr;
+    sp.desc = reinterpret_cast<uint64_t *>(base + VL.desc);
+    sp.ticket = reinterpret_cast<uint32_t *>(base + VL.hdr);
+    sp.status = status;
+    sp.n_tiles = VL.n_tiles;
+    sp.stall_tile = -1;
+    sp.wait_ns = static_cast<uint64_t>(g_wait_ns.load());
+    k_scan<false><<<static_cast<unsigned>(VL.n_tiles), kScanThreads, 0, stream>>>(sp);
+    if (count_only) return cudaGetLastError() == cudaSuccess ? VOX_OK : VOX_ERR_CUDA;
+    k_bin_scatter<<<static_cast<unsigned>(bin_blocks), 256, 0, stream>>>(bp);
+    BrickParams brp;
+    brp.segs = bp.segs;
+    brp.G = G;
+    brp.brick_off = bp.brick_off;
+    brp.pieces = bp.pieces;
+    brp.capacity = capacity;
+    brp.mask = mask;
+    brp.status = status;
+    brp.ticket = reinterpret_cast<uint32_t *>(base + VL.hdr + 128);
+    const int per_sm = blocks_per_sm(reinterpret_cast<const void *>(k_brick_volume), kBrickThreads, 0);
+    if (per_sm <= 0) return VOX_ERR_CUDA;
+    k_brick_volume<<<static_cast<unsigned>(per_sm * sms), kBrickThreads, 0, stream>>>(brp);
+    if (cudaGetLastError() != cudaSuccess) return VOX_ERR_CUDA;
+    return launch_generate(segs, n, dims, nullptr, 0, mask, VOX_OUT_BITMASK, ws, status, stream,
+                           bp.brick_off + G.n_bricks, capacity);
+}
+
+// All requested outputs of one scene, after the count + scan: the list by the
+// voxel-parallel kernel; the volume by brick ownership when the workspace holds
+// the brick arrays (vox_workspace_size_volume), else by per-voxel atomics.
+vox_status launch_outputs(const vox_segment *segs, int64_t n, vox_dims dims, void *list, int64_t capacity,
+                          uint32_t *mask, int flags, void *ws, size_t ws_bytes, int32_t *status, cudaStream_t stream)
+{
+    if (n == 0) return VOX_OK;
+    BrickGeom G;
+    const bool bm = flags & VOX_OUT_BITMASK;
+    const bool bricks = bm && make_geom(dims, &G) && ws_bytes >= vol_layout(n, G, 1).total;
+    if (!bricks) return launch_generate(segs, n, dims, list, capacity, mask, flags, ws, status, stream);
+    const int list_flags = flags & (VOX_OUT_LIST32 | VOX_OUT_LIST64);
+    if (list_flags) {
+        if (vox_status e = launch_generate(segs, n, dims, list, capacity, nullptr, list_flags, ws, status, stream))
+            return e;
+    }
+    return launch_bricks(segs, n, G, dims, mask, ws, ws_bytes, status, stream);
 }
 
 // ---- allocation-free variant: scratch in a static device array -------------
@@ -291,7 +432,7 @@ vox_status vox_generate(const vox_segment *d_segs, int64_t n, vox_dims dims, voi
     if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), s) != cudaSuccess) return VOX_ERR_CUDA;
     if (n == 0) return VOX_OK;
     if (vox_status e = launch_count_scan(d_segs, n, dims, nullptr, nullptr, d_ws, d_status, s)) return e;
-    return launch_generate(d_segs, n, dims, d_list, list_capacity, d_mask, flags, d_ws, d_status, s);
+    return launch_outputs(d_segs, n, dims, d_list, list_capacity, d_mask, flags, d_ws, ws_bytes, d_status, s);
 }
 
 vox_status vox_generate_from_scan(const vox_segment *d_segs, int64_t n, vox_dims dims, void *d_list,
@@ -301,8 +442,48 @@ vox_status vox_generate_from_scan(const vox_segment *d_segs, int64_t n, vox_dims
     if (vox_status e = check_generate_args(d_segs, n, dims, d_list, list_capacity, d_mask, flags, d_ws, ws_bytes,
                                            d_status))
         return e;
-    return launch_generate(d_segs, n, dims, d_list, list_capacity, d_mask, flags, d_ws, d_status,
-                           static_cast<cudaStream_t>(stream));
+    return launch_outputs(d_segs, n, dims, d_list, list_capacity, d_mask, flags, d_ws, ws_bytes, d_status,
+                          static_cast<cudaStream_t>(stream));
+}
+
+size_t vox_workspace_size_volume(int64_t n, vox_dims dims, int64_t piece_capacity)
+{
+    if (n < 0 || piece_capacity < 0) return 0;
+    BrickGeom G;
+    if (!make_geom(dims, &G)) return ws_layout(n).total;
+    return vol_layout(n, G, piece_capacity > 0 ? piece_capacity : 1).total;
+}
+
+vox_status vox_plan(const vox_segment *d_segs, int64_t n, vox_dims dims, void *d_ws, size_t ws_bytes,
+                    int32_t *d_status, int64_t *h_voxels, int64_t *h_pieces, void *stream)
+{
+    if (n < 0 || d_status == nullptr || (n > 0 && d_segs == nullptr)) return VOX_ERR_INVALID_ARG;
+    if (vox_status e = check_dims(dims)) return e;
+    if (n > 0 && !aligned(d_segs, 16)) return VOX_ERR_ALIGNMENT;
+    BrickGeom G;
+    const bool bricks = make_geom(dims, &G);
+    const size_t need = bricks ? vol_layout(n, G, 0).total : ws_layout(n).total;
+    if (d_ws == nullptr || !aligned(d_ws, kWsAlign) || ws_bytes < need) return VOX_ERR_WORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (vox_status e = vox_count(d_segs, n, dims, nullptr, nullptr, d_ws, ws_bytes, d_status, s)) return e;
+    int64_t V = 0, pieces = 0;
+    int32_t st = 0;
+    if (n > 0 && bricks) {
+        if (vox_status e = launch_bricks(d_segs, n, G, dims, nullptr, d_ws, ws_bytes, d_status, s, true)) return e;
+        const VolLayout VL = vol_layout(n, G, 0);
+        if (cudaMemcpyAsync(&pieces, static_cast<char *>(d_ws) + VL.off + 8 * static_cast<size_t>(G.n_bricks),
+                            sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return VOX_ERR_CUDA;
+    }
+    const WsLayout L = ws_layout(n);
+    if (cudaMemcpyAsync(&V, static_cast<char *>(d_ws) + L.offsets + sizeof(int64_t) * static_cast<size_t>(n),
+                        sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return VOX_ERR_CUDA;
+    if (cudaMemcpyAsync(&st, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return VOX_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return VOX_ERR_CUDA;
+    if (h_voxels) *h_voxels = V;
+    if (h_pieces) *h_pieces = pieces;
+    return static_cast<vox_status>(st);
 }
 
 size_t vox_host_arena_size(int64_t n, vox_dims dims, int flags, int64_t list_capacity)

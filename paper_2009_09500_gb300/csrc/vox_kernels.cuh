@@ -1,6 +1,6 @@
 // vox_kernels.cuh -- the three kernels of the voxelization hot path (sm_103a):
 //
-//   k_count_scan  per-segment voxel count N + 1 (+ endpoint validation) fused
+//   k_scan        per-segment voxel count N + 1 (+ endpoint validation) fused
 //                 with a single-pass decoupled look-back exclusive scan
 //                 (Merrill & Garland, 2016) into int64 offsets;
 //   k_generate    voxel-parallel generation: each CTA owns a contiguous range of
@@ -43,7 +43,9 @@ constexpr int32_t kStCapacity = 4;
 constexpr int32_t kStTimeout = 5;
 
 struct ScanParams {
-    const int32_t *segs;  // [n][6]
+    const int32_t *segs;       // [n][6] (segment counts) or null
+    const int32_t *counts_in;  // [n] (plain counts) or null
+    int64_t *offsets_copy;     // [n] second copy of the exclusive offsets, or null
     int64_t n;
     int32_t w, h, d;
     int32_t *counts;       // [n] or null
@@ -58,7 +60,10 @@ struct ScanParams {
 };
 
 // ---------------------------------------------------------------- count + scan
-__global__ void __launch_bounds__(kScanThreads) k_count_scan(ScanParams p)
+// kFromSegments: the counts are N + 1 of each segment (with endpoint checks);
+// otherwise they are read from p.counts_in (e.g. pieces per brick).
+template <bool kFromSegments>
+__global__ void __launch_bounds__(kScanThreads) k_scan(ScanParams p)
 {
     __shared__ __align__(16) int32_t s_cnt[kScanTile];
     __shared__ int64_t s_loc[kScanTile];
@@ -82,7 +87,9 @@ __global__ void __launch_bounds__(kScanThreads) k_count_scan(ScanParams p)
         const int idx = j * kScanThreads + t;
         const int64_t s = base + idx;
         int32_t c = 0;
-        if (s < p.n) {
+        if (!kFromSegments) {
+            if (s < p.n) c = __ldg(p.counts_in + s);
+        } else if (s < p.n) {
             const int2 *r = reinterpret_cast<const int2 *>(p.segs + 6 * s);
             const int2 a = __ldg(r), b = __ldg(r + 1), e = __ldg(r + 2);
             const int32_t x0 = a.x, y0 = a.y, z0 = b.x, x1 = b.y, y1 = e.x, z1 = e.y;
@@ -193,6 +200,7 @@ __global__ void __launch_bounds__(kScanThreads) k_count_scan(ScanParams p)
             const int64_t o = excl + s_loc[idx];
             p.offsets[s] = o;
             if (p.offsets_out) p.offsets_out[s] = o;
+            if (p.offsets_copy) p.offsets_copy[s] = o;
         }
     }
     if (tile == p.n_tiles - 1 && t == 0) {
@@ -220,6 +228,8 @@ struct GenParams {
     int32_t *status;
     uint64_t wait_ns;
     int64_t min_per_cta;     // smallest voxel range worth a CTA (multiple of 4)
+    const int64_t *gate_total;  // if set, run only when *gate_total > gate_cap
+    int64_t gate_cap;
 };
 
 // Shared memory of k_generate: the staged window of segments and, for list
@@ -315,6 +325,7 @@ __global__ void __launch_bounds__(kGenThreads) k_generate(GenParams p)
     // prologue decided by one thread so that the whole CTA agrees
     if (t == 0) {
         int32_t go = ld_volatile_i32(p.status) == 0;  // an earlier error: write nothing
+        if (p.gate_total != nullptr && __ldg(p.gate_total) <= p.gate_cap) go = 0;  // brick path took it
         const int64_t V = __ldg(p.offsets + p.n);
         if (go && kList && V > p.capacity) {
             set_status(p.status, kStCapacity);

@@ -37,6 +37,7 @@ EXPORTED = (
     "vox_workspace_size", "vox_count", "vox_generate", "vox_generate_from_scan",
     "vox_host_arena_size", "vox_generate_host", "vox_strerror", "vox_mask_words",
     "vox_debug_set_scan_stall", "vox_scan_tile_segments", "vox_generate_noalloc",
+    "vox_workspace_size_volume", "vox_plan",
 )
 NOALLOC_MAX_SEGMENTS = 2000000
 
@@ -92,6 +93,10 @@ def load(path: str | None = None):
     lib.vox_debug_set_scan_stall.restype = None
     lib.vox_scan_tile_segments.argtypes = []
     lib.vox_scan_tile_segments.restype = i64
+    lib.vox_workspace_size_volume.argtypes = [i64, Dims, i64]
+    lib.vox_workspace_size_volume.restype = sz
+    lib.vox_plan.argtypes = [vp, i64, Dims, vp, sz, vp, vp, vp, vp]
+    lib.vox_plan.restype = i32
     lib.vox_generate_noalloc.argtypes = [vp, i64, Dims, vp, i64, vp, i32, vp, vp]
     lib.vox_generate_noalloc.restype = i32
     if path == _build.LIB:
@@ -129,6 +134,22 @@ def _check(st: int, where: str):
 
 def vox_workspace_size(n: int) -> int:
     return int(load().vox_workspace_size(int(n)))
+
+
+def vox_workspace_size_volume(n: int, dims, piece_capacity: int) -> int:
+    return int(load().vox_workspace_size_volume(int(n), _dims(dims), int(piece_capacity)))
+
+
+def vox_plan(segs, dims, ws, status, stream=None):
+    """Synchronous: returns (V, pieces) for these segments (pieces = 0 when the
+    volume cannot use bricks). ``ws`` must hold vox_workspace_size_volume(n, dims, 0)."""
+    _check_segs(segs)
+    V = ctypes.c_int64(0)
+    P = ctypes.c_int64(0)
+    st = load().vox_plan(_ptr(segs), segs.shape[0], _dims(dims), _ptr(ws), ws.numel() * ws.element_size(),
+                         _ptr(status), ctypes.byref(V), ctypes.byref(P), _stream(stream))
+    _check(st, "vox_plan")
+    return int(V.value), int(P.value)
 
 
 def vox_mask_words(dims) -> int:

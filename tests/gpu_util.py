@@ -14,14 +14,24 @@ SENTINEL32 = -0x21524111  # 0xDEADBEEF as int32
 SENTINEL64 = -0x2152411021524111
 
 
-def run_gpu(segs_np, dims, flags, capacity=None, extra=64, mask_init=None, use_from_scan=False):
+def run_gpu(segs_np, dims, flags, capacity=None, extra=64, mask_init=None, use_from_scan=False, pieces=None):
     """vox_count then vox_generate (or vox_generate_from_scan) on cuda:0.
     The list gets ``extra`` sentinel elements past the capacity the call is told
-    about, to catch writes beyond it."""
+    about, to catch writes beyond it. ``pieces``: None for the plain workspace
+    (per-voxel atomic volume), "plan" to size the brick workspace with vox_plan,
+    or an explicit piece capacity."""
     segs = torch.from_numpy(np.ascontiguousarray(segs_np, dtype=np.int32)).cuda()
     n = segs.shape[0]
-    ws = torch.empty(vox.vox_workspace_size(n), dtype=torch.uint8, device="cuda")
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    planned = None
+    if pieces is None:
+        ws = torch.empty(vox.vox_workspace_size(n), dtype=torch.uint8, device="cuda")
+    else:
+        ws = torch.empty(vox.vox_workspace_size_volume(n, dims, 0), dtype=torch.uint8, device="cuda")
+        if n:
+            planned = vox.vox_plan(segs, dims, ws, status)
+        cap = planned[1] if pieces == "plan" else int(pieces)
+        ws = torch.empty(vox.vox_workspace_size_volume(n, dims, cap), dtype=torch.uint8, device="cuda")
     counts = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
     offsets = torch.empty(n + 1, dtype=torch.int64, device="cuda")
     vox.vox_count(segs, dims, ws, status, counts[:n] if n else None, offsets)
@@ -31,7 +41,7 @@ def run_gpu(segs_np, dims, flags, capacity=None, extra=64, mask_init=None, use_f
     if capacity is None:
         capacity = V
     res = {"count_status": count_status, "V": V, "counts": counts[:n].cpu().numpy(),
-           "offsets": offsets.cpu().numpy(), "capacity": capacity}
+           "offsets": offsets.cpu().numpy(), "capacity": capacity, "planned": planned}
     list_t = None
     if flags & vox.OUT_LIST64:
         list_t = torch.full((capacity + extra,), SENTINEL64, dtype=torch.int64, device="cuda")
@@ -101,3 +111,25 @@ def check_mask_sparse(mask_t: torch.Tensor, words: np.ndarray, bits: np.ndarray)
 
 def get_oracle():
     return oracle.get()
+
+
+def brick_pieces_expected(O, segs, dims):
+    """Number of brick pieces (maximal runs of a segment's voxels inside one
+    brick) from the oracle's voxels and the documented brick shape: B0 = min(w,
+    256), then the largest power-of-two rows B1 x B2 (B1 = 2 B2 or B2) with
+    B0/32 * B1 * B2 <= 8192 words."""
+    w = int(dims[0])
+    b0 = min(w, 256)
+    rows = 8192 // (b0 // 32)
+    p2 = 1
+    while (2 * p2) ** 2 <= rows:
+        p2 *= 2
+    b1 = 2 * p2 if 2 * p2 * p2 <= rows else p2
+    B = np.array([b0, b1, p2])
+    xyz = O.voxels_xyz(segs)
+    counts = O.count(segs).astype(np.int64)
+    starts = np.zeros(len(xyz), dtype=bool)
+    starts[np.concatenate([[0], np.cumsum(counts)[:-1]])] = True
+    bc = xyz // B
+    change = np.any(bc[1:] != bc[:-1], axis=1) & ~starts[1:]
+    return int(starts.sum() + change.sum())

@@ -10,8 +10,8 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_util import (assert_list_equal, check_mask_sparse, get_oracle, oracle_list, run_gpu,
-                      sparse_mask_from_list64)
+from gpu_util import (assert_list_equal, brick_pieces_expected, check_mask_sparse, get_oracle, oracle_list,
+                      run_gpu, sparse_mask_from_list64)
 from paper_2009_09500_gb300 import vox, workloads
 
 pytestmark = pytest.mark.gpu
@@ -337,3 +337,102 @@ def test_repeated_calls_are_stable():
     r2 = run_gpu(w.segs, w.dims, L32 | BM)
     assert np.array_equal(r1["list_full"], r2["list_full"])
     assert np.array_equal(r1["mask"], r2["mask"])
+
+
+# ------------------------------------------------------- volume by brick ownership
+@pytest.mark.parametrize("flags", [BM, L32 | BM, L64 | BM])
+def test_bricks_config1(flags):
+    w = workloads.config1()
+    r = full_check(w.segs, w.dims, flags, pieces="plan")
+    V, P = r["planned"]
+    assert V == r["V"] and P == brick_pieces_expected(get_oracle(), w.segs, w.dims)
+
+
+def test_bricks_config2_full_size():
+    """The benchmarked workload with the brick-built volume, whole outputs compared."""
+    w = workloads.config2()
+    r = full_check(w.segs, w.dims, L32 | BM, pieces="plan")
+    assert r["planned"][1] > w.n
+
+
+@pytest.mark.parametrize("dims", [(64, 64, 64), (96, 40, 17), (32, 7, 5), (128, 128, 64), (256, 8, 300)])
+def test_bricks_volume_shapes(dims):
+    rng = np.random.default_rng(sum(dims))
+    segs = workloads.uniform_segments(rng, 3000, dims)
+    r = full_check(segs, dims, BM, pieces="plan")
+    assert r["planned"][1] == brick_pieces_expected(get_oracle(), segs, dims)
+
+
+def test_bricks_fallback_when_pieces_do_not_fit():
+    """Too small a piece capacity: the call falls back to atomics on the device,
+    same bits."""
+    w = workloads.config1()
+    full_check(w.segs, w.dims, L32 | BM, pieces=100)
+
+
+def test_bricks_width_not_multiple_of_32_uses_atomics():
+    rng = np.random.default_rng(15)
+    dims = (13, 7, 5)
+    segs = workloads.uniform_segments(rng, 2000, dims)
+    r = full_check(segs, dims, BM, pieces="plan")
+    assert r["planned"][1] == 0
+
+
+def test_bricks_or_into_and_degenerate():
+    rng = np.random.default_rng(16)
+    dims = (64, 64, 64)
+    p0 = rng.integers(0, 64, size=(3000, 3)).astype(np.int32)
+    segs = np.concatenate([np.concatenate([p0, p0], axis=1), workloads.uniform_segments(rng, 500, dims)])
+    init = rng.integers(0, 2**32, size=vox.vox_mask_words(dims), dtype=np.uint64).astype(np.uint32)
+    init[::2] = 0
+    full_check(segs, dims, BM, pieces="plan", mask_init=init)
+
+
+def test_bricks_config3_prefix_sparse():
+    w = workloads.config3(n=60000)
+    O = get_oracle()
+    segs = torch.from_numpy(w.segs).cuda()
+    n = w.n
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ws = torch.empty(vox.vox_workspace_size_volume(n, w.dims, 0), dtype=torch.uint8, device="cuda")
+    V, P = vox.vox_plan(segs, w.dims, ws, status)
+    ws = torch.empty(vox.vox_workspace_size_volume(n, w.dims, P), dtype=torch.uint8, device="cuda")
+    mask = torch.zeros(vox.vox_mask_words(w.dims), dtype=torch.int32, device="cuda")
+    vox.vox_generate(segs, w.dims, ws, status, None, mask)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    words, bits = sparse_mask_from_list64(O.list64(w.segs), w.dims)
+    check_mask_sparse(mask, words, bits)
+
+
+def test_bricks_config3_full_size_sampled():
+    """All 4M log-uniform segments, 8 GiB volume built by bricks: sampled
+    segments' voxels must be set, and the set-bit count must equal the atomic
+    path's on the same input."""
+    w = workloads.config3()
+    O = get_oracle()
+    segs = torch.from_numpy(w.segs).cuda()
+    n = w.n
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ws = torch.empty(vox.vox_workspace_size_volume(n, w.dims, 0), dtype=torch.uint8, device="cuda")
+    V, P = vox.vox_plan(segs, w.dims, ws, status)
+    ws = torch.empty(vox.vox_workspace_size_volume(n, w.dims, P), dtype=torch.uint8, device="cuda")
+    mask = torch.zeros(vox.vox_mask_words(w.dims), dtype=torch.int32, device="cuda")
+    vox.vox_generate(segs, w.dims, ws, status, None, mask)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    rng = np.random.default_rng(98)
+    sample = rng.integers(0, n, size=2000)
+    want = np.concatenate([O.list64(w.segs[s:s + 1]) for s in sample])
+    words, bits = sparse_mask_from_list64(want, w.dims)
+    m = mask[torch.from_numpy(words).cuda()].cpu().numpy().view(np.uint32)
+    assert ((m & bits) == bits).all()
+    del ws
+    ws2 = torch.empty(vox.vox_workspace_size(n), dtype=torch.uint8, device="cuda")
+    mask2 = torch.zeros_like(mask)
+    vox.vox_generate(segs, w.dims, ws2, status, None, mask2)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    assert torch.equal(mask, mask2), "brick and atomic volumes differ"
+    del mask, mask2
+    torch.cuda.empty_cache()
