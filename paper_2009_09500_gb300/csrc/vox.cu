@@ -2,6 +2,8 @@
 // workspace layout, kernel selection and launches. Host code only calls the
 // CUDA runtime for launches, stream-ordered memsets/copies and device queries;
 // it allocates no device memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -130,12 +132,123 @@ vox_status check_generate_args(const vox_segment *segs, int64_t n, vox_dims dims
     return VOX_OK;
 }
 
+// ---- the volume by brick ownership ------------------------------------------
+constexpr int64_t kMaxBricks = int64_t(1) << 26;
+
+// Brick shape for a volume whose rows are whole 32-bit words (w % 32 == 0):
+// B0 = min(w, 256) voxels along x (whole words), then B1 x B2 rows (powers of
+// two) so that a brick has at most kBrickWordsMax words.
+bool make_geom(vox_dims dims, BrickGeom *G)
+{
+    if (check_dims(dims) != VOX_OK || dims.w % 32 != 0) return false;
+    int32_t b0 = 32;  // the largest 32 * 2^k not above min(w, 256)
+    while (2 * b0 <= dims.w && 2 * b0 <= 256) b0 *= 2;
+    G->B[0] = b0;
+    G->bxw = b0 / 32;
+    G->log_bxw = 0;
+    while ((1 << G->log_bxw) < G->bxw) ++G->log_bxw;
+    const int32_t rows = kBrickWordsMax / G->bxw;
+    int32_t p2 = 1;
+    while ((2 * p2) * (2 * p2) <= rows) p2 *= 2;
+    G->B[1] = (2 * p2 * p2 <= rows) ? 2 * p2 : p2;
+    G->B[2] = p2;
+    G->log_b1 = 0;
+    while ((1 << G->log_b1) < G->B[1]) ++G->log_b1;
+    G->dim[0] = dims.w;
+    G->dim[1] = dims.h;
+    G->dim[2] = dims.d;
+    G->row_words = dims.w / 32;
+    G->words = G->bxw * G->B[1] * G->B[2];
+    int64_t nb = 1;
+    for (int a = 0; a < 3; ++a) {
+        G->nb[a] = (G->dim[a] + G->B[a] - 1) / G->B[a];
+        nb *= G->nb[a];
+    }
+    G->n_bricks = nb;
+    return nb <= kMaxBricks && G->words <= kBrickWordsMax;
+}
+
+// Tensor map of the volume as a 3-D array of 32-bit words (row_words x h x d)
+// with brick-sized boxes, for the TMA reduce-OR merge. Needs 16-byte aligned
+// rows and box rows (w and B0 multiples of 128) and a 16-byte aligned volume.
+bool make_volume_tmap(const BrickGeom &G, uint32_t *mask, CUtensorMap *out)
+{
+    if (G.bxw % 4 != 0 || G.row_words % 4 != 0 || !aligned(mask, 16)) return false;
+    static std::mutex mu;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (encode == nullptr) {
+            void *fn = nullptr;
+            cudaDriverEntryPointQueryResult q;
+            if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                    cudaSuccess ||
+                q != cudaDriverEntryPointSuccess || fn == nullptr)
+                return false;
+            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        }
+    }
+    const cuuint64_t dims[3] = {static_cast<cuuint64_t>(G.row_words), static_cast<cuuint64_t>(G.dim[1]),
+                                static_cast<cuuint64_t>(G.dim[2])};
+    const cuuint64_t strides[2] = {4ull * G.row_words, 4ull * G.row_words * static_cast<cuuint64_t>(G.dim[1])};
+    const cuuint32_t box[3] = {static_cast<cuuint32_t>(G.bxw), static_cast<cuuint32_t>(G.B[1]),
+                               static_cast<cuuint32_t>(G.B[2])};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (box[1] > 256 || box[2] > 256) return false;
+    return encode(out, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, mask, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+struct VolLayout {
+    int64_t n_tiles;  // scan tiles over the brick counts
+    size_t hdr;       // scan ticket at +0, brick ticket at +128
+    size_t count;     // int32 [n_bricks]
+    size_t desc;      // uint64 [n_tiles]
+    size_t off;       // int64 [n_bricks + 4]
+    size_t cursor;    // int64 [n_bricks + 1]
+    size_t pieces;    // uint64 [capacity]
+    size_t total;
+};
+
+// The volume path's workspace follows the base layout of ws_layout(n).
+VolLayout vol_layout(int64_t n, const BrickGeom &G, int64_t capacity)
+{
+    VolLayout L;
+    const size_t nb = static_cast<size_t>(G.n_bricks);
+    L.n_tiles = (G.n_bricks + kScanTile - 1) / kScanTile;
+    L.hdr = ws_layout(n).total;
+    L.count = L.hdr + kWsAlign;
+    L.desc = L.count + align_up(4 * nb);
+    L.off = L.desc + align_up(8 * static_cast<size_t>(L.n_tiles));
+    L.cursor = L.off + align_up(8 * (nb + 4));
+    L.pieces = L.cursor + align_up(8 * (nb + 1));
+    L.total = L.pieces + align_up(8 * static_cast<size_t>(capacity));
+    return L;
+}
+
+// Whether a call on n segments with this workspace builds the volume by brick
+// ownership (the workspace holds the brick arrays and room for a piece).
+bool uses_bricks(int64_t n, vox_dims dims, size_t ws_bytes, BrickGeom *G)
+{
+    return n > 0 && make_geom(dims, G) && ws_bytes >= vol_layout(n, *G, 1).total;
+}
+
+// Count + scan. With a brick workspace it also zeroes the brick arrays and
+// counts every segment's pieces per brick (k_bin_count).
 vox_status launch_count_scan(const vox_segment *segs, int64_t n, vox_dims dims, int32_t *counts,
-                             int64_t *offsets_out, void *ws, int32_t *status, cudaStream_t stream)
+                             int64_t *offsets_out, void *ws, size_t ws_bytes, int32_t *status, cudaStream_t stream)
 {
     const WsLayout L = ws_layout(n);
     char *base = static_cast<char *>(ws);
     if (cudaMemsetAsync(base, 0, L.offsets, stream) != cudaSuccess) return VOX_ERR_CUDA;
+    BrickGeom G;
+    const bool bins = uses_bricks(n, dims, ws_bytes, &G);
+    VolLayout VL{};
+    if (bins) {
+        VL = vol_layout(n, G, 0);
+        if (cudaMemsetAsync(base + VL.hdr, 0, VL.off - VL.hdr, stream) != cudaSuccess) return VOX_ERR_CUDA;
+    }
     ScanParams p;
     p.segs = reinterpret_cast<const int32_t *>(segs);
     p.counts_in = nullptr;
@@ -154,6 +267,16 @@ vox_status launch_count_scan(const vox_segment *segs, int64_t n, vox_dims dims, 
     p.stall_tile = g_stall_tile.load();
     p.wait_ns = static_cast<uint64_t>(g_wait_ns.load());
     k_scan<true><<<static_cast<unsigned>(L.n_tiles), kScanThreads, 0, stream>>>(p);
+    if (bins) {
+        BinParams bp{};
+        bp.segs = p.segs;
+        bp.n = n;
+        bp.G = G;
+        bp.brick_count = reinterpret_cast<int32_t *>(base + VL.count);
+        bp.status = status;
+        const unsigned blocks = static_cast<unsigned>((n + 255) / 256);
+        k_bin_count<<<blocks, 256, 0, stream>>>(bp);
+    }
     return cudaGetLastError() == cudaSuccess ? VOX_OK : VOX_ERR_CUDA;
 }
 
@@ -206,72 +329,19 @@ vox_status launch_generate(const vox_segment *segs, int64_t n, vox_dims dims, vo
     return lin64 ? launch_gen_t<kOutMask, true>(p, stream) : launch_gen_t<kOutMask, false>(p, stream);
 }
 
-// ---- the volume by brick ownership ------------------------------------------
-constexpr int64_t kMaxBricks = int64_t(1) << 26;
-
-// Brick shape for a volume whose rows are whole 32-bit words (w % 32 == 0):
-// B0 = min(w, 256) voxels along x (whole words), then B1 x B2 rows (powers of
-// two) so that a brick has at most kBrickWordsMax words.
-bool make_geom(vox_dims dims, BrickGeom *G)
-{
-    if (check_dims(dims) != VOX_OK || dims.w % 32 != 0) return false;
-    G->B[0] = dims.w < 256 ? dims.w : 256;
-    G->bxw = G->B[0] / 32;
-    const int32_t rows = kBrickWordsMax / G->bxw;
-    int32_t p2 = 1;
-    while ((2 * p2) * (2 * p2) <= rows) p2 *= 2;
-    G->B[1] = (2 * p2 * p2 <= rows) ? 2 * p2 : p2;
-    G->B[2] = p2;
-    G->dim[0] = dims.w;
-    G->dim[1] = dims.h;
-    G->dim[2] = dims.d;
-    G->row_words = dims.w / 32;
-    G->words = G->bxw * G->B[1] * G->B[2];
-    int64_t nb = 1;
-    for (int a = 0; a < 3; ++a) {
-        G->nb[a] = (G->dim[a] + G->B[a] - 1) / G->B[a];
-        nb *= G->nb[a];
-    }
-    G->n_bricks = nb;
-    return nb <= kMaxBricks && G->words <= kBrickWordsMax;
-}
-
-struct VolLayout {
-    int64_t n_tiles;  // scan tiles over the brick counts
-    size_t hdr;       // scan ticket at +0, brick ticket at +128
-    size_t count;     // int32 [n_bricks]
-    size_t desc;      // uint64 [n_tiles]
-    size_t off;       // int64 [n_bricks + 4]
-    size_t cursor;    // int64 [n_bricks + 1]
-    size_t pieces;    // uint64 [capacity]
-    size_t total;
-};
-
-// The volume path's workspace follows the base layout of ws_layout(n).
-VolLayout vol_layout(int64_t n, const BrickGeom &G, int64_t capacity)
-{
-    VolLayout L;
-    const size_t nb = static_cast<size_t>(G.n_bricks);
-    L.n_tiles = (G.n_bricks + kScanTile - 1) / kScanTile;
-    L.hdr = ws_layout(n).total;
-    L.count = L.hdr + kWsAlign;
-    L.desc = L.count + align_up(4 * nb);
-    L.off = L.desc + align_up(8 * static_cast<size_t>(L.n_tiles));
-    L.cursor = L.off + align_up(8 * (nb + 4));
-    L.pieces = L.cursor + align_up(8 * (nb + 1));
-    L.total = L.pieces + align_up(8 * static_cast<size_t>(capacity));
-    return L;
-}
-
 // bin -> scan -> scatter -> per-brick volume, then the atomic kernel, which only
 // runs if the pieces did not fit in the workspace
 vox_status launch_bricks(const vox_segment *segs, int64_t n, const BrickGeom &G, vox_dims dims, uint32_t *mask,
                          void *ws, size_t ws_bytes, int32_t *status, cudaStream_t stream, bool count_only = false)
 {
+    // the brick counts come from the count + scan (k_bin_count); the
+    // tickets and look-back flags of this pass are reset here, so that the pass
+    // can run again on the same counts
     const VolLayout VL = vol_layout(n, G, 0);
     const int64_t capacity = static_cast<int64_t>((ws_bytes - VL.pieces) / 8);
     char *base = static_cast<char *>(ws);
-    if (cudaMemsetAsync(base + VL.hdr, 0, VL.off - VL.hdr, stream) != cudaSuccess) return VOX_ERR_CUDA;
+    if (cudaMemsetAsync(base + VL.hdr, 0, kWsAlign, stream) != cudaSuccess) return VOX_ERR_CUDA;
+    if (cudaMemsetAsync(base + VL.desc, 0, VL.off - VL.desc, stream) != cudaSuccess) return VOX_ERR_CUDA;
     BinParams bp;
     bp.segs = reinterpret_cast<const int32_t *>(segs);
     bp.n = n;
@@ -284,9 +354,7 @@ vox_status launch_bricks(const vox_segment *segs, int64_t n, const BrickGeom &G,
     bp.status = status;
     const int sms = sm_count();
     if (sms <= 0) return VOX_ERR_CUDA;
-    int64_t bin_blocks = (n + 255) / 256;
-    if (bin_blocks > 8 * sms) bin_blocks = 8 * sms;
-    k_bin_count<<<static_cast<unsigned>(bin_blocks), 256, 0, stream>>>(bp);
+    const int64_t bin_blocks = (n + 255) / 256;
     ScanParams sp;
     sp.segs = nullptr;
     sp.counts_in = bp.brick_count;
@@ -314,9 +382,14 @@ vox_status launch_bricks(const vox_segment *segs, int64_t n, const BrickGeom &G,
     brp.mask = mask;
     brp.status = status;
     brp.ticket = reinterpret_cast<uint32_t *>(base + VL.hdr + 128);
-    const int per_sm = blocks_per_sm(reinterpret_cast<const void *>(k_brick_volume), kBrickThreads, 0);
+    CUtensorMap tmap;
+    std::memset(&tmap, 0, sizeof(tmap));
+    brp.use_tma = (mask != nullptr && make_volume_tmap(G, mask, &tmap)) ? 1 : 0;
+    const size_t bsmem = sizeof(BrickSmem);
+    if (vox_status e = allow_smem(reinterpret_cast<const void *>(k_brick_volume), bsmem)) return e;
+    const int per_sm = blocks_per_sm(reinterpret_cast<const void *>(k_brick_volume), kBrickThreads, bsmem);
     if (per_sm <= 0) return VOX_ERR_CUDA;
-    k_brick_volume<<<static_cast<unsigned>(per_sm * sms), kBrickThreads, 0, stream>>>(brp);
+    k_brick_volume<<<static_cast<unsigned>(per_sm * sms), kBrickThreads, bsmem, stream>>>(brp, tmap);
     if (cudaGetLastError() != cudaSuccess) return VOX_ERR_CUDA;
     return launch_generate(segs, n, dims, nullptr, 0, mask, VOX_OUT_BITMASK, ws, status, stream,
                            bp.brick_off + G.n_bricks, capacity);
@@ -331,7 +404,7 @@ vox_status launch_outputs(const vox_segment *segs, int64_t n, vox_dims dims, voi
     if (n == 0) return VOX_OK;
     BrickGeom G;
     const bool bm = flags & VOX_OUT_BITMASK;
-    const bool bricks = bm && make_geom(dims, &G) && ws_bytes >= vol_layout(n, G, 1).total;
+    const bool bricks = bm && uses_bricks(n, dims, ws_bytes, &G);
     if (!bricks) return launch_generate(segs, n, dims, list, capacity, mask, flags, ws, status, stream);
     const int list_flags = flags & (VOX_OUT_LIST32 | VOX_OUT_LIST64);
     if (list_flags) {
@@ -419,7 +492,7 @@ vox_status vox_count(const vox_segment *d_segs, int64_t n, vox_dims dims, int32_
         if (d_offsets && cudaMemsetAsync(d_offsets, 0, sizeof(int64_t), s) != cudaSuccess) return VOX_ERR_CUDA;
         return VOX_OK;
     }
-    return launch_count_scan(d_segs, n, dims, d_counts, d_offsets, d_ws, d_status, s);
+    return launch_count_scan(d_segs, n, dims, d_counts, d_offsets, d_ws, ws_bytes, d_status, s);
 }
 
 vox_status vox_generate(const vox_segment *d_segs, int64_t n, vox_dims dims, void *d_list, int64_t list_capacity,
@@ -431,7 +504,7 @@ vox_status vox_generate(const vox_segment *d_segs, int64_t n, vox_dims dims, voi
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), s) != cudaSuccess) return VOX_ERR_CUDA;
     if (n == 0) return VOX_OK;
-    if (vox_status e = launch_count_scan(d_segs, n, dims, nullptr, nullptr, d_ws, d_status, s)) return e;
+    if (vox_status e = launch_count_scan(d_segs, n, dims, nullptr, nullptr, d_ws, ws_bytes, d_status, s)) return e;
     return launch_outputs(d_segs, n, dims, d_list, list_capacity, d_mask, flags, d_ws, ws_bytes, d_status, s);
 }
 
@@ -461,9 +534,10 @@ vox_status vox_plan(const vox_segment *d_segs, int64_t n, vox_dims dims, void *d
     if (vox_status e = check_dims(dims)) return e;
     if (n > 0 && !aligned(d_segs, 16)) return VOX_ERR_ALIGNMENT;
     BrickGeom G;
-    const bool bricks = make_geom(dims, &G);
-    const size_t need = bricks ? vol_layout(n, G, 0).total : ws_layout(n).total;
+    const bool brickable = make_geom(dims, &G);
+    const size_t need = brickable ? vol_layout(n, G, 1).total : ws_layout(n).total;
     if (d_ws == nullptr || !aligned(d_ws, kWsAlign) || ws_bytes < need) return VOX_ERR_WORKSPACE;
+    const bool bricks = n > 0 && brickable;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (vox_status e = vox_count(d_segs, n, dims, nullptr, nullptr, d_ws, ws_bytes, d_status, s)) return e;
     int64_t V = 0, pieces = 0;

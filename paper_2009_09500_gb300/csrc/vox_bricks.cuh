@@ -22,6 +22,8 @@
 // q(k) = floor((2 k A + N) / (2 N)) first reaches Q at k = ceil(N (2Q - 1) / (2A)).
 #pragma once
 
+#include <cuda.h>
+
 #include <cstdint>
 
 #include "vox_device.cuh"
@@ -33,9 +35,11 @@ constexpr int kBrickWordsMax = 8192;  // 32 KB shared bitmap per brick
 constexpr int32_t kNoStep = 0x7fffffff;
 
 struct BrickGeom {
-    int32_t B[3];       // brick extent in voxels per axis (B[0] a multiple of 32)
+    int32_t B[3];       // brick extent in voxels per axis (powers of two, B[0] >= 32)
     int32_t nb[3];      // bricks per axis
     int32_t bxw;        // words per brick row, B[0] / 32
+    int32_t log_bxw;    // log2(bxw)
+    int32_t log_b1;     // log2(B[1])
     int32_t row_words;  // words per volume row, w / 32
     int32_t dim[3];     // volume extent
     int32_t words;      // words per brick, bxw * B[1] * B[2]
@@ -141,33 +145,30 @@ __device__ __forceinline__ void load_record(const int32_t *segs, int64_t s, int3
     r[0] = a.x; r[1] = a.y; r[2] = b.x; r[3] = b.y; r[4] = c.x; r[5] = c.y;
 }
 
+// One segment per thread.
 __global__ void __launch_bounds__(256) k_bin_count(BinParams p)
 {
-    if (ld_volatile_i32(p.status) != 0) return;
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    for (int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; s < p.n; s += stride) {
-        int32_t r[6];
-        load_record(p.segs, s, r);
-        if (!endpoints_inside(r, p.G)) continue;  // reported by the count kernel
-        for_each_piece(r, p.G, [&](int64_t b, int32_t, int32_t) { atomicAdd(p.brick_count + b, 1); });
-    }
+    const int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (s >= p.n || ld_volatile_i32(p.status) != 0) return;
+    int32_t r[6];
+    load_record(p.segs, s, r);
+    if (!endpoints_inside(r, p.G)) return;  // reported by the count kernel
+    for_each_piece(r, p.G, [&](int64_t b, int32_t, int32_t) { atomicAdd(p.brick_count + b, 1); });
 }
 
+// One segment per thread.
 __global__ void __launch_bounds__(256) k_bin_scatter(BinParams p)
 {
-    if (ld_volatile_i32(p.status) != 0) return;
+    const int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (s >= p.n || ld_volatile_i32(p.status) != 0) return;
     if (__ldg(p.brick_off + p.G.n_bricks) > p.capacity) return;  // the volume falls back to atomics
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    for (int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; s < p.n; s += stride) {
-        int32_t r[6];
-        load_record(p.segs, s, r);
-        if (!endpoints_inside(r, p.G)) continue;
-        for_each_piece(r, p.G, [&](int64_t b, int32_t k, int32_t len) {
-            const unsigned long long pos =
-                atomicAdd(reinterpret_cast<unsigned long long *>(p.cursor + b), 1ull);
-            p.pieces[pos] = pack_piece(s, k, len);
-        });
-    }
+    int32_t r[6];
+    load_record(p.segs, s, r);
+    if (!endpoints_inside(r, p.G)) return;
+    for_each_piece(r, p.G, [&](int64_t b, int32_t k, int32_t len) {
+        const unsigned long long pos = atomicAdd(reinterpret_cast<unsigned long long *>(p.cursor + b), 1ull);
+        p.pieces[pos] = pack_piece(s, k, len);
+    });
 }
 
 struct BrickParams {
@@ -179,12 +180,87 @@ struct BrickParams {
     uint32_t *mask;
     const int32_t *status;
     uint32_t *ticket;  // zeroed before launch
+    int32_t use_tma;   // merge by one TMA tensor reduce-OR per brick (tensor map valid)
 };
 
-__global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p)
+// TMA tensor reduction of a whole brick tile from shared memory into the volume:
+// every word of the box (bxw x B1 x B2 words at word coordinates x, y, z) is
+// OR-ed into global memory by the L2, asynchronously; parts of the box outside
+// the volume are skipped by the hardware.
+__device__ __forceinline__ void tma_reduce_or_3d(const CUtensorMap *tmap, const void *smem, int32_t x, int32_t y,
+                                                 int32_t z)
 {
-    __shared__ __align__(16) uint32_t bits[kBrickWordsMax];
-    __shared__ int64_t s_brick;
+    asm volatile(
+        "cp.reduce.async.bulk.tensor.3d.global.shared::cta.or.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+            reinterpret_cast<uint64_t>(tmap)),
+        "r"(x), "r"(y), "r"(z), "r"(smem_addr(smem))
+        : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Merge a brick's shared bitmap into the volume. Brick row (ly, lz) holds bxw
+// words that are contiguous in the volume; a warp covers 32 consecutive words.
+// Only touched words are read and written. Eight independent loads per thread
+// are issued before the stores, so DRAM latency is paid once per group, not
+// once per word. The brick owns its words: plain loads and stores suffice.
+__device__ __forceinline__ void merge_brick(const uint32_t *bits, const BrickGeom &G, int32_t X0, int32_t Y0,
+                                            int32_t Z0, uint32_t *mask)
+{
+    constexpr int kGroup = 8;
+    const int t = threadIdx.x;
+    for (int q0 = 0; q0 < G.words; q0 += kGroup * kBrickThreads) {
+        uint32_t v[kGroup], old[kGroup];
+        int64_t gw[kGroup];
+#pragma unroll
+        for (int e = 0; e < kGroup; ++e) {
+            const int q = q0 + e * kBrickThreads + t;
+            v[e] = 0;
+            gw[e] = 0;
+            if (q < G.words) {
+                const uint32_t b = bits[q];
+                const int32_t row = q >> G.log_bxw, col = q & (G.bxw - 1);
+                const int32_t y = Y0 + (row & (G.B[1] - 1)), z = Z0 + (row >> G.log_b1);
+                if (b != 0 && y < G.dim[1] && z < G.dim[2] && X0 / 32 + col < G.row_words) {
+                    v[e] = b;
+                    gw[e] = X0 / 32 + col + static_cast<int64_t>(G.row_words) * (y + static_cast<int64_t>(G.dim[1]) * z);
+                }
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < kGroup; ++e) old[e] = v[e] ? mask[gw[e]] : 0u;
+#pragma unroll
+        for (int e = 0; e < kGroup; ++e)
+            if (v[e]) mask[gw[e]] = old[e] | v[e];
+    }
+}
+
+constexpr int kChunk = 512;        // pieces staged per round (with their segment records)
+constexpr int kLenClasses = 11;    // piece length classes: floor(log2(len)), len <= 1024
+
+struct BrickSmem {
+    alignas(128) uint32_t bits[kBrickWordsMax];  // also the TMA source tile (128-byte aligned)
+    alignas(16) int32_t rec[kChunk * 6];
+    uint64_t pc[kChunk];
+    uint16_t order[kChunk];
+    int32_t cls[2 * kLenClasses];  // counts, then cursors
+    int32_t origin[3];
+    int64_t brick;
+};
+
+// One CTA per brick (dynamic tickets). Pieces are staged kChunk at a time with
+// their segment records; inside a chunk they are grouped by length class
+// (floor(log2(len))) so that the 32 lanes of a warp, one piece each, walk pieces
+// of similar length. Each lane enters its piece's segment at the piece's first
+// step (one division per minor axis) and steps through it with the carry
+// recurrence, OR-ing bits into the brick's shared bitmap.
+__global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, const __grid_constant__ CUtensorMap tmap)
+{
+    static_assert(kChunk == 2 * kBrickThreads, "two pieces per thread per chunk");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    BrickSmem &sm = *reinterpret_cast<BrickSmem *>(smem_raw);
     const int t = threadIdx.x;
     if (ld_volatile_i32(p.status) != 0) return;
     if (__ldg(p.brick_off + p.G.n_bricks) > p.capacity) return;  // pieces did not fit: atomics path
@@ -192,62 +268,100 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p)
     const uint32_t bw = static_cast<uint32_t>(G.B[0]);
     const uint32_t bwh = static_cast<uint32_t>(G.B[0]) * static_cast<uint32_t>(G.B[1]);
     while (true) {
-        if (t == 0) s_brick = atomicAdd(p.ticket, 1u);
+        if (t == 0) {
+            const int64_t b = atomicAdd(p.ticket, 1u);
+            sm.brick = b;
+            if (b < G.n_bricks) {
+                const int64_t rest = b / G.nb[0];
+                sm.origin[0] = static_cast<int32_t>(b - rest * G.nb[0]) * G.B[0];
+                sm.origin[1] = static_cast<int32_t>(rest % G.nb[1]) * G.B[1];
+                sm.origin[2] = static_cast<int32_t>(rest / G.nb[1]) * G.B[2];
+            }
+        }
         __syncthreads();
-        const int64_t b = s_brick;
-        __syncthreads();  // s_brick is rewritten only after everyone has read it
+        const int64_t b = sm.brick;
+        const int32_t X0 = sm.origin[0], Y0 = sm.origin[1], Z0 = sm.origin[2];
+        __syncthreads();  // the ticket slot is rewritten only after everyone has read it
         if (b >= G.n_bricks) break;
         const int64_t lo = __ldg(p.brick_off + b), hi = __ldg(p.brick_off + b + 1);
         if (lo == hi) continue;
-        const int32_t i0 = static_cast<int32_t>(b % G.nb[0]);
-        const int64_t rest = b / G.nb[0];
-        const int32_t i1 = static_cast<int32_t>(rest % G.nb[1]);
-        const int32_t i2 = static_cast<int32_t>(rest / G.nb[1]);
-        const int32_t X0 = i0 * G.B[0], Y0 = i1 * G.B[1], Z0 = i2 * G.B[2];
-        for (int q = t; q < G.words; q += kBrickThreads) bits[q] = 0u;
-        __syncthreads();
+        if (p.use_tma) {  // the previous brick's reduction must have read the tile
+            if (t == 0) bulk_wait_read_all();
+            __syncthreads();
+        }
+        for (int q = t; q < G.words; q += kBrickThreads) sm.bits[q] = 0u;
         // brick-local bit index of (x, y, z): (x - X0) + B0 (y - Y0) + B0 B1 (z - Z0),
         // kept modulo 2^32 while stepping (only the local value is ever used)
         const uint32_t origin = static_cast<uint32_t>(X0) + static_cast<uint32_t>(Y0) * bw +
                                 static_cast<uint32_t>(Z0) * bwh;
-        for (int64_t pi = lo + t; pi < hi; pi += kBrickThreads) {
-            const uint64_t pc = __ldg(p.pieces + pi);
-            const int64_t seg = static_cast<int64_t>(pc & 0xffffffffull);
-            const int32_t k_lo = static_cast<int32_t>((pc >> 32) & 0x3fffffull);
-            const int32_t len = static_cast<int32_t>(pc >> 54) + 1;
-            int32_t r[6];
-            load_record(p.segs, seg, r);
-            Stepper<uint32_t, uint32_t> st;
-            st.enter(r, k_lo, bw, bwh);
-            st.L -= origin;
-            uint32_t cur = 0xffffffffu, acc = 0;
-            for (int32_t e = 0; e < len; ++e) {
-                const uint32_t word = st.L >> 5;
-                if (word != cur) {
-                    if (acc) atomicOr(bits + cur, acc);
-                    cur = word;
-                    acc = 0;
+        for (int64_t c0 = lo; c0 < hi; c0 += kChunk) {
+            const int32_t cnt = static_cast<int32_t>(min(static_cast<int64_t>(kChunk), hi - c0));
+            if (t < 2 * kLenClasses) sm.cls[t] = 0;
+            __syncthreads();  // previous chunk done, class counters cleared
+            // ---- stage the chunk and count pieces per length class
+            int32_t cls2[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int i = t + e * kBrickThreads;
+                cls2[e] = -1;
+                if (i < cnt) {
+                    const uint64_t pc = __ldg(p.pieces + c0 + i);
+                    sm.pc[i] = pc;
+                    const uint32_t len = static_cast<uint32_t>(pc >> 54) + 1u;
+                    cls2[e] = 31 - __clz(len);
+                    atomicAdd(sm.cls + cls2[e], 1);
+                    load_record(p.segs, static_cast<int64_t>(pc & 0xffffffffull), sm.rec + 6 * i);
                 }
-                acc |= 1u << (st.L & 31u);
-                st.template step<false, true>();
             }
-            if (acc) atomicOr(bits + cur, acc);
+            __syncthreads();
+            if (t == 0) {
+                int32_t run = 0;
+                for (int c = 0; c < kLenClasses; ++c) {
+                    sm.cls[kLenClasses + c] = run;
+                    run += sm.cls[c];
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int e = 0; e < 2; ++e)
+                if (cls2[e] >= 0) sm.order[atomicAdd(sm.cls + kLenClasses + cls2[e], 1)] = static_cast<uint16_t>(t + e * kBrickThreads);
+            __syncthreads();
+            // ---- one piece per lane, in class order
+#pragma unroll 1
+            for (int j = t; j < cnt; j += kBrickThreads) {
+                const int i = sm.order[j];
+                const uint64_t pc = sm.pc[i];
+                const int32_t len = static_cast<int32_t>(pc >> 54) + 1;
+                Stepper<uint32_t, uint32_t> st;
+                st.enter(sm.rec + 6 * i, static_cast<int32_t>((pc >> 32) & 0x3fffffull), bw, bwh);
+                uint32_t L = st.L - origin;
+                st.L = L;
+                uint32_t cur = L >> 5, acc = 0;
+                for (int32_t e = 0; e < len; ++e) {
+                    const uint32_t word = st.L >> 5;
+                    if (word != cur) {
+                        atomicOr(sm.bits + cur, acc);
+                        cur = word;
+                        acc = 0;
+                    }
+                    acc |= 1u << (st.L & 31u);
+                    st.template step<false, true>();
+                }
+                atomicOr(sm.bits + cur, acc);
+            }
         }
         __syncthreads();
-        // merge into the volume: brick row (ly, lz) holds bxw words that are
-        // contiguous in the volume; only touched words are read and written
-        for (int q = t; q < G.words; q += kBrickThreads) {
-            const uint32_t v = bits[q];
-            if (v == 0) continue;
-            const int32_t row = q / G.bxw, col = q - row * G.bxw;
-            const int32_t y = Y0 + row % G.B[1], z = Z0 + row / G.B[1];
-            if (y >= G.dim[1] || z >= G.dim[2] || X0 / 32 + col >= G.row_words) continue;
-            const int64_t gw = X0 / 32 + col + static_cast<int64_t>(G.row_words) *
-                                                    (y + static_cast<int64_t>(G.dim[1]) * z);
-            p.mask[gw] |= v;  // the brick owns these words: no other writer
+        if (p.use_tma) {
+            if (t == 0) {
+                fence_proxy_async_smem();  // the bitmap's generic writes, visible to the TMA unit
+                tma_reduce_or_3d(&tmap, sm.bits, X0 / 32, Y0, Z0);
+            }
+        } else {
+            merge_brick(sm.bits, G, X0, Y0, Z0, p.mask);
+            __syncthreads();
         }
-        __syncthreads();
     }
+    if (p.use_tma && t == 0) bulk_wait_all();  // reductions complete before the CTA's memory goes
 }
 
 }  // namespace vox

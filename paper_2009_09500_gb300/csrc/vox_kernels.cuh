@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(ScanParams p)
     if (t == 0) s_tile = atomicAdd(p.ticket, 1u);
     __syncthreads();
     const int64_t tile = s_tile;
+    if (tile >= p.n_tiles) return;  // only if the ticket was not reset: publish nothing
     const int64_t base = tile * kScanTile;
 
     // counts, read in a strided (coalesced) order

@@ -436,3 +436,23 @@ def test_bricks_config3_full_size_sampled():
     assert torch.equal(mask, mask2), "brick and atomic volumes differ"
     del mask, mask2
     torch.cuda.empty_cache()
+
+
+def test_bricks_generation_repeated_after_one_count():
+    """vox_count once, then the volume pass twice (fresh volumes): both exact.
+    The brick pass resets its own tickets, so it can run again on the counts."""
+    w = workloads.config1()
+    O = get_oracle()
+    segs = torch.from_numpy(w.segs).cuda()
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ws = torch.empty(vox.vox_workspace_size_volume(w.n, w.dims, 0), dtype=torch.uint8, device="cuda")
+    V, P = vox.vox_plan(segs, w.dims, ws, status)
+    ws = torch.empty(vox.vox_workspace_size_volume(w.n, w.dims, P), dtype=torch.uint8, device="cuda")
+    vox.vox_count(segs, w.dims, ws, status)
+    want = O.bitmask(w.segs, w.dims)
+    for _ in range(2):
+        mask = torch.zeros(vox.vox_mask_words(w.dims), dtype=torch.int32, device="cuda")
+        vox.vox_generate_from_scan(segs, w.dims, ws, status, None, mask, BM)
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0
+        assert np.array_equal(mask.cpu().numpy().view(np.uint32), want)
