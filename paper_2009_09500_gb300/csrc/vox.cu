@@ -165,6 +165,8 @@ bool make_geom(vox_dims dims, BrickGeom *G)
         nb *= G->nb[a];
     }
     G->n_bricks = nb;
+    G->reps = nb <= 32768 ? 8 : 1;
+    G->n_slots = nb * G->reps;
     return nb <= kMaxBricks && G->words <= kBrickWordsMax;
 }
 
@@ -203,10 +205,10 @@ bool make_volume_tmap(const BrickGeom &G, uint32_t *mask, CUtensorMap *out)
 struct VolLayout {
     int64_t n_tiles;  // scan tiles over the brick counts
     size_t hdr;       // scan ticket at +0, brick ticket at +128
-    size_t count;     // int32 [n_bricks]
+    size_t count;     // int32 [n_slots]
     size_t desc;      // uint64 [n_tiles]
-    size_t off;       // int64 [n_bricks + 4]
-    size_t cursor;    // int64 [n_bricks + 1]
+    size_t off;       // int64 [n_slots + 4]
+    size_t cursor;    // int64 [n_slots + 1]
     size_t pieces;    // uint64 [capacity]
     size_t total;
 };
@@ -215,8 +217,8 @@ struct VolLayout {
 VolLayout vol_layout(int64_t n, const BrickGeom &G, int64_t capacity)
 {
     VolLayout L;
-    const size_t nb = static_cast<size_t>(G.n_bricks);
-    L.n_tiles = (G.n_bricks + kScanTile - 1) / kScanTile;
+    const size_t nb = static_cast<size_t>(G.n_slots);
+    L.n_tiles = (G.n_slots + kScanTile - 1) / kScanTile;
     L.hdr = ws_layout(n).total;
     L.count = L.hdr + kWsAlign;
     L.desc = L.count + align_up(4 * nb);
@@ -359,7 +361,7 @@ vox_status launch_bricks(const vox_segment *segs, int64_t n, const BrickGeom &G,
     sp.segs = nullptr;
     sp.counts_in = bp.brick_count;
     sp.offsets_copy = bp.cursor;
-    sp.n = G.n_bricks;
+    sp.n = G.n_slots;
     sp.w = sp.h = sp.d = 0;
     sp.counts = nullptr;
     sp.offsets = reinterpret_cast<int64_t *>(base + VL.off);
@@ -392,7 +394,7 @@ vox_status launch_bricks(const vox_segment *segs, int64_t n, const BrickGeom &G,
     k_brick_volume<<<static_cast<unsigned>(per_sm * sms), kBrickThreads, bsmem, stream>>>(brp, tmap);
     if (cudaGetLastError() != cudaSuccess) return VOX_ERR_CUDA;
     return launch_generate(segs, n, dims, nullptr, 0, mask, VOX_OUT_BITMASK, ws, status, stream,
-                           bp.brick_off + G.n_bricks, capacity);
+                           bp.brick_off + G.n_slots, capacity);
 }
 
 // All requested outputs of one scene, after the count + scan: the list by the
@@ -545,7 +547,7 @@ vox_status vox_plan(const vox_segment *d_segs, int64_t n, vox_dims dims, void *d
     if (n > 0 && bricks) {
         if (vox_status e = launch_bricks(d_segs, n, G, dims, nullptr, d_ws, ws_bytes, d_status, s, true)) return e;
         const VolLayout VL = vol_layout(n, G, 0);
-        if (cudaMemcpyAsync(&pieces, static_cast<char *>(d_ws) + VL.off + 8 * static_cast<size_t>(G.n_bricks),
+        if (cudaMemcpyAsync(&pieces, static_cast<char *>(d_ws) + VL.off + 8 * static_cast<size_t>(G.n_slots),
                             sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
             return VOX_ERR_CUDA;
     }

@@ -44,6 +44,12 @@ struct BrickGeom {
     int32_t dim[3];     // volume extent
     int32_t words;      // words per brick, bxw * B[1] * B[2]
     int64_t n_bricks;
+    // Each brick has `reps` counters / cursors (segment s uses replica s % reps),
+    // brick-major, so that a brick's pieces stay contiguous after the scan while
+    // the atomics on one brick spread over `reps` addresses (few bricks, many
+    // pieces each: the counters would otherwise serialise).
+    int32_t reps;
+    int64_t n_slots;    // n_bricks * reps
 };
 
 __device__ __forceinline__ int64_t brick_index(const BrickGeom &G, int32_t b0, int32_t b1, int32_t b2)
@@ -130,9 +136,9 @@ struct BinParams {
     const int32_t *segs;
     int64_t n;
     BrickGeom G;
-    int32_t *brick_count;     // [n_bricks], zeroed before k_bin_count
-    int64_t *cursor;          // [n_bricks], exclusive offsets (k_bin_scatter bumps them)
-    const int64_t *brick_off; // [n_bricks + 1]; brick_off[n_bricks] = number of pieces
+    int32_t *brick_count;     // [n_slots], zeroed before k_bin_count
+    int64_t *cursor;          // [n_slots], exclusive offsets (k_bin_scatter bumps them)
+    const int64_t *brick_off; // [n_slots + 1]; brick_off[n_slots] = number of pieces
     uint64_t *pieces;         // [capacity]
     int64_t capacity;
     const int32_t *status;
@@ -153,7 +159,8 @@ __global__ void __launch_bounds__(256) k_bin_count(BinParams p)
     int32_t r[6];
     load_record(p.segs, s, r);
     if (!endpoints_inside(r, p.G)) return;  // reported by the count kernel
-    for_each_piece(r, p.G, [&](int64_t b, int32_t, int32_t) { atomicAdd(p.brick_count + b, 1); });
+    const int32_t rep = static_cast<int32_t>(s % p.G.reps);
+    for_each_piece(r, p.G, [&](int64_t b, int32_t, int32_t) { atomicAdd(p.brick_count + b * p.G.reps + rep, 1); });
 }
 
 // One segment per thread.
@@ -161,20 +168,43 @@ __global__ void __launch_bounds__(256) k_bin_scatter(BinParams p)
 {
     const int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (s >= p.n || ld_volatile_i32(p.status) != 0) return;
-    if (__ldg(p.brick_off + p.G.n_bricks) > p.capacity) return;  // the volume falls back to atomics
+    if (__ldg(p.brick_off + p.G.n_slots) > p.capacity) return;  // the volume falls back to atomics
+    const int32_t rep = static_cast<int32_t>(s % p.G.reps);
     int32_t r[6];
     load_record(p.segs, s, r);
     if (!endpoints_inside(r, p.G)) return;
+    // slot reservations of up to four pieces are in flight together before
+    // their stores, so the returning atomics' latency overlaps
+    constexpr int kBatch = 4;
+    int64_t bb[kBatch];
+    uint64_t val[kBatch];
+    int nb = 0;
+    auto flush = [&]() {
+        unsigned long long pos[kBatch];
+#pragma unroll
+        for (int e = 0; e < kBatch; ++e)
+            if (e < nb) pos[e] = atomicAdd(reinterpret_cast<unsigned long long *>(p.cursor + bb[e]), 1ull);
+#pragma unroll
+        for (int e = 0; e < kBatch; ++e)
+            if (e < nb) p.pieces[pos[e]] = val[e];
+        nb = 0;
+    };
     for_each_piece(r, p.G, [&](int64_t b, int32_t k, int32_t len) {
-        const unsigned long long pos = atomicAdd(reinterpret_cast<unsigned long long *>(p.cursor + b), 1ull);
-        p.pieces[pos] = pack_piece(s, k, len);
+#pragma unroll
+        for (int e = 0; e < kBatch; ++e)
+            if (e == nb) {
+                bb[e] = b * p.G.reps + rep;
+                val[e] = pack_piece(s, k, len);
+            }
+        if (++nb == kBatch) flush();
     });
+    if (nb) flush();
 }
 
 struct BrickParams {
     const int32_t *segs;
     BrickGeom G;
-    const int64_t *brick_off;  // [n_bricks + 1]
+    const int64_t *brick_off;  // [n_slots + 1]
     const uint64_t *pieces;
     int64_t capacity;
     uint32_t *mask;
@@ -247,23 +277,26 @@ struct BrickSmem {
     uint16_t order[kChunk];
     int32_t cls[2 * kLenClasses];  // counts, then cursors
     int32_t origin[3];
+    int32_t next_group;            // next group of 32 ordered pieces to hand to a warp
     int64_t brick;
 };
 
 // One CTA per brick (dynamic tickets). Pieces are staged kChunk at a time with
-// their segment records; inside a chunk they are grouped by length class
-// (floor(log2(len))) so that the 32 lanes of a warp, one piece each, walk pieces
-// of similar length. Each lane enters its piece's segment at the piece's first
-// step (one division per minor axis) and steps through it with the carry
-// recurrence, OR-ing bits into the brick's shared bitmap.
+// their segment records; inside a chunk they are ordered by length class
+// (floor(log2(len))), longest first, and warps take groups of 32 consecutive
+// pieces from a shared counter: the 32 lanes of a warp walk pieces of similar
+// length, and the warps share the chunk's work as it comes (longest groups
+// first, so the tail is short). Each lane enters its piece's segment at the
+// piece's first step (one division per minor axis) and steps through it with
+// the carry recurrence, OR-ing bits into the brick's shared bitmap.
 __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, const __grid_constant__ CUtensorMap tmap)
 {
     static_assert(kChunk == 2 * kBrickThreads, "two pieces per thread per chunk");
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    BrickSmem &sm = *reinterpret_cast<BrickSmem *>(smem_raw);
+    extern __shared__ __align__(128) unsigned char brick_smem_raw[];
+    BrickSmem &sm = *reinterpret_cast<BrickSmem *>(brick_smem_raw);
     const int t = threadIdx.x;
     if (ld_volatile_i32(p.status) != 0) return;
-    if (__ldg(p.brick_off + p.G.n_bricks) > p.capacity) return;  // pieces did not fit: atomics path
+    if (__ldg(p.brick_off + p.G.n_slots) > p.capacity) return;  // pieces did not fit: atomics path
     const BrickGeom &G = p.G;
     const uint32_t bw = static_cast<uint32_t>(G.B[0]);
     const uint32_t bwh = static_cast<uint32_t>(G.B[0]) * static_cast<uint32_t>(G.B[1]);
@@ -283,7 +316,7 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
         const int32_t X0 = sm.origin[0], Y0 = sm.origin[1], Z0 = sm.origin[2];
         __syncthreads();  // the ticket slot is rewritten only after everyone has read it
         if (b >= G.n_bricks) break;
-        const int64_t lo = __ldg(p.brick_off + b), hi = __ldg(p.brick_off + b + 1);
+        const int64_t lo = __ldg(p.brick_off + b * G.reps), hi = __ldg(p.brick_off + (b + 1) * G.reps);
         if (lo == hi) continue;
         if (p.use_tma) {  // the previous brick's reduction must have read the tile
             if (t == 0) bulk_wait_read_all();
@@ -316,38 +349,41 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
             __syncthreads();
             if (t == 0) {
                 int32_t run = 0;
-                for (int c = 0; c < kLenClasses; ++c) {
+                for (int c = kLenClasses - 1; c >= 0; --c) {  // longest class first
                     sm.cls[kLenClasses + c] = run;
                     run += sm.cls[c];
                 }
+                sm.next_group = 0;
             }
             __syncthreads();
 #pragma unroll
             for (int e = 0; e < 2; ++e)
                 if (cls2[e] >= 0) sm.order[atomicAdd(sm.cls + kLenClasses + cls2[e], 1)] = static_cast<uint16_t>(t + e * kBrickThreads);
             __syncthreads();
-            // ---- one piece per lane, in class order
+            // ---- one piece per lane; warps take groups of 32 ordered pieces
+            const int lane = t & 31;
 #pragma unroll 1
-            for (int j = t; j < cnt; j += kBrickThreads) {
-                const int i = sm.order[j];
-                const uint64_t pc = sm.pc[i];
-                const int32_t len = static_cast<int32_t>(pc >> 54) + 1;
-                Stepper<uint32_t, uint32_t> st;
-                st.enter(sm.rec + 6 * i, static_cast<int32_t>((pc >> 32) & 0x3fffffull), bw, bwh);
-                uint32_t L = st.L - origin;
-                st.L = L;
-                uint32_t cur = L >> 5, acc = 0;
-                for (int32_t e = 0; e < len; ++e) {
-                    const uint32_t word = st.L >> 5;
-                    if (word != cur) {
-                        atomicOr(sm.bits + cur, acc);
-                        cur = word;
-                        acc = 0;
+            while (true) {
+                int32_t grp = 0;
+                if (lane == 0) grp = atomicAdd(&sm.next_group, 1);
+                grp = __shfl_sync(0xffffffffu, grp, 0);
+                if (grp * 32 >= cnt) break;
+                const int j = grp * 32 + lane;
+                if (j < cnt) {
+                    const int i = sm.order[j];
+                    const uint64_t pc = sm.pc[i];
+                    const int32_t len = static_cast<int32_t>(pc >> 54) + 1;
+                    Stepper<uint32_t, uint32_t> st;
+                    st.enter(sm.rec + 6 * i, static_cast<int32_t>((pc >> 32) & 0x3fffffull), bw, bwh);
+                    st.L -= origin;
+                    // one shared-memory atomic per voxel: cheaper than branching to
+                    // merge runs of the same word (measured on both workload shapes)
+                    for (int32_t e = 0; e < len; ++e) {
+                        atomicOr(sm.bits + (st.L >> 5), 1u << (st.L & 31u));
+                        st.template step<false, true>();
                     }
-                    acc |= 1u << (st.L & 31u);
-                    st.template step<false, true>();
                 }
-                atomicOr(sm.bits + cur, acc);
+                __syncwarp();
             }
         }
         __syncthreads();
