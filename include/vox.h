@@ -168,6 +168,52 @@ vox_status vox_plan(const vox_segment *d_segs, int64_t n, vox_dims dims, void *d
                     int32_t *d_status, int64_t *h_voxels, int64_t *h_pieces, void *stream);
 
 /*
+ * Batched scenes (many independent problems in one launch sequence, Section 5's
+ * conclusion 3: few kernel calls, many segments per call).
+ *
+ * A batch is one segment array holding the scenes' segments back to back, and a
+ * DEVICE table of n_scenes vox_scene entries: scene k covers segments
+ * [seg_begin, seg_begin + n), seg_begin of scene 0 is 0, each scene starts where
+ * the previous one ends, and the last ends at n_total (checked on the device:
+ * VOX_ERR_INVALID_ARG in *d_status, nothing written).
+ */
+typedef struct vox_scene {
+    int64_t seg_begin; /* first segment of the scene in the batch's segment array */
+    int64_t n;         /* segments of the scene */
+    vox_dims dims;     /* the scene's volume extent (each in [1, 2^21]) */
+    int32_t reserved;  /* must be 0 */
+    uint32_t *mask;    /* the scene's volume (ceil(w*h*d/32) words, OR-ed into), or NULL */
+} vox_scene;           /* 40 bytes */
+
+/* Workspace bytes for a batch of n_total segments in n_scenes scenes. */
+size_t vox_workspace_size_batched(int64_t n_total, int32_t n_scenes);
+
+/*
+ * vox_generate_batched -- count, scan and generate every scene of a batch with
+ * one launch per step (scene map, count + scan, scene bases, list, volumes),
+ * whatever the number of scenes; suitable for capture in a CUDA graph.
+ *   d_segs          device vox_segment[n_total], 16-byte aligned
+ *   d_scenes        device vox_scene[n_scenes], 8-byte aligned
+ *   d_list          ONE list for the whole batch (LIST32 or LIST64 in flags):
+ *                   scene k's voxels are at [base[k], base[k+1]), in segment
+ *                   order, k = 0..N per segment; list_capacity elements; every
+ *                   scene must have edges <= 1024 for LIST32
+ *   flags           list format and/or VOX_OUT_BITMASK (each scene's voxels are
+ *                   OR-ed into that scene's mask; scenes with mask NULL skip it)
+ *   d_scene_base    device int64[n_scenes + 1] receiving base[k] (first voxel of
+ *                   scene k in the list) and base[n_scenes] = total V, or NULL
+ *   d_ws, ws_bytes  at least vox_workspace_size_batched(n_total, n_scenes)
+ *   d_status        as for vox_generate
+ * The volumes are built by per-voxel deduplicated atomic ORs over voxel tiles
+ * dealt round-robin to the CTAs, so that the scenes in flight at any moment are
+ * few and their volumes stay in L2.
+ */
+vox_status vox_generate_batched(const vox_segment *d_segs, int64_t n_total, const vox_scene *d_scenes,
+                                int32_t n_scenes, void *d_list, int64_t list_capacity, int flags,
+                                int64_t *d_scene_base, void *d_ws, size_t ws_bytes, int32_t *d_status,
+                                void *stream);
+
+/*
  * vox_generate_host -- vox_generate on host buffers, copies included (the
  * host-device pipeline of Fig. 4: input copy, kernels, result copy back).
  * SYNCHRONOUS: returns once the results are in host memory (it synchronises

@@ -1,0 +1,168 @@
+"""Batched scenes: many independent voxelization problems in one launch
+sequence (vox_generate_batched), optionally captured once in a CUDA graph and
+replayed.
+
+Section 5 of the paper ends on this point: single-segment calls waste the GPU on
+call and copy overheads, and throughput comes from voxelizing many segments per
+kernel call. Here a batch concatenates the scenes' segments, keeps one device
+scene table, one list for the whole batch (scene k at [base[k], base[k+1])) and
+one volume per scene. All device memory is allocated by torch; the work runs in
+libvox's kernels.
+"""
+
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import vox
+
+
+class SceneRecord(ctypes.Structure):
+    """Host image of vox_scene (include/vox.h), 40 bytes."""
+
+    _fields_ = [("seg_begin", ctypes.c_int64), ("n", ctypes.c_int64), ("dims", vox.Dims),
+                ("reserved", ctypes.c_int32), ("mask", ctypes.c_void_p)]
+
+
+assert ctypes.sizeof(SceneRecord) == 40
+
+
+def scene_table_bytes(seg_counts, dims_list, mask_ptrs) -> bytes:
+    """Pack a vox_scene array: contiguous scenes in order."""
+    n = len(seg_counts)
+    arr = (SceneRecord * n)()
+    begin = 0
+    for k in range(n):
+        arr[k].seg_begin = begin
+        arr[k].n = int(seg_counts[k])
+        w, h, d = (int(v) for v in dims_list[k])
+        arr[k].dims = vox.Dims(w, h, d)
+        arr[k].reserved = 0
+        arr[k].mask = int(mask_ptrs[k]) if mask_ptrs[k] else None
+        begin += int(seg_counts[k])
+    return bytes(arr)
+
+
+@dataclass
+class Batch:
+    """A batch resident on the device: segments, scene table, list, volumes, workspace."""
+
+    segs: object          # int32 [n_total, 6] (cuda)
+    scenes: object        # uint8 [40 * n_scenes] (cuda), the vox_scene table
+    n_scenes: int
+    dims: list
+    seg_counts: list
+    masks: list           # int32 volume tensors (cuda), one per scene
+    lst: object           # int32 / int64 list for the whole batch, or None
+    scene_base: object    # int64 [n_scenes + 1] (cuda)
+    ws: object
+    status: object
+    flags: int
+    V: int
+
+    def run(self, stream=None):
+        """Enqueue the batched launch sequence on `stream` (asynchronous)."""
+        st = vox.load().vox_generate_batched(
+            vox._ptr(self.segs), self.segs.shape[0], vox._ptr(self.scenes), self.n_scenes,
+            vox._ptr(self.lst), self.lst.numel() if self.lst is not None else 0, self.flags,
+            vox._ptr(self.scene_base), vox._ptr(self.ws), self.ws.numel(), vox._ptr(self.status),
+            vox._stream(stream))
+        if st != vox.OK:
+            raise vox.VoxError(st, "vox_generate_batched")
+
+    def clear_volumes(self):
+        for m in self.masks:
+            m.zero_()
+
+    def scene_list(self, k: int):
+        """View of scene k's voxels in the batch list (after a synchronised run)."""
+        b = self.scene_base.cpu().numpy()
+        return self.lst[int(b[k]):int(b[k + 1])]
+
+
+def make_batch(workloads_list, flags=vox.OUT_LIST32 | vox.OUT_BITMASK, device="cuda") -> Batch:
+    """Upload scenes (workloads.Workload objects) as one batch. The list is sized
+    exactly (from the segments' voxel counts, summed here on the host from the
+    same input bytes; the device recounts and checks the capacity)."""
+    import torch
+
+    segs_np = np.ascontiguousarray(np.concatenate([w.segs for w in workloads_list], axis=0), dtype=np.int32)
+    seg_counts = [w.n for w in workloads_list]
+    dims = [tuple(w.dims) for w in workloads_list]
+    d = np.abs(segs_np[:, 3:].astype(np.int64) - segs_np[:, :3])
+    V = int((d.max(axis=1) + 1).sum()) if len(segs_np) else 0
+    masks = []
+    if flags & vox.OUT_BITMASK:
+        masks = [torch.zeros(vox.vox_mask_words(dm), dtype=torch.int32, device=device) for dm in dims]
+    ptrs = [m.data_ptr() for m in masks] if masks else [0] * len(dims)
+    table = scene_table_bytes(seg_counts, dims, ptrs)
+    scenes = torch.frombuffer(bytearray(table), dtype=torch.uint8).to(device)
+    lst = None
+    if flags & vox.OUT_LIST64:
+        lst = torch.empty(max(V, 1), dtype=torch.int64, device=device)
+    elif flags & vox.OUT_LIST32:
+        lst = torch.empty(max(V, 1), dtype=torch.int32, device=device)
+    n_scenes = len(workloads_list)
+    ws = torch.empty(vox.vox_workspace_size_batched(len(segs_np), n_scenes), dtype=torch.uint8, device=device)
+    return Batch(segs=torch.from_numpy(segs_np).to(device), scenes=scenes, n_scenes=n_scenes, dims=dims,
+                 seg_counts=seg_counts, masks=masks, lst=lst,
+                 scene_base=torch.zeros(n_scenes + 1, dtype=torch.int64, device=device), ws=ws,
+                 status=torch.zeros(1, dtype=torch.int32, device=device), flags=flags, V=V)
+
+
+class GraphRunner:
+    """Capture a launch sequence once (torch.cuda.CUDAGraph) and replay it."""
+
+    def __init__(self, fn, warmup: int = 1):
+        import torch
+
+        self.stream = torch.cuda.Stream()
+        self.stream.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(self.stream):
+            for _ in range(warmup):
+                fn(self.stream)
+        torch.cuda.current_stream().wait_stream(self.stream)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=self.stream):
+            fn(self.stream)
+        torch.cuda.synchronize()
+
+    def replay(self):
+        self.graph.replay()
+
+
+class PlainScenes:
+    """The same scenes, one vox_generate per scene (the plain per-scene launch),
+    with per-scene workspaces sized for the brick volume path."""
+
+    def __init__(self, batch: Batch, device="cuda"):
+        import torch
+
+        self.batch = batch
+        self.items = []
+        segs = batch.segs
+        begin = 0
+        for k in range(batch.n_scenes):
+            n = batch.seg_counts[k]
+            s = segs[begin:begin + n].clone()  # own, 16-byte aligned copy
+            dims = batch.dims[k]
+            ws0 = torch.empty(vox.vox_workspace_size_volume(n, dims, 0), dtype=torch.uint8, device=device)
+            V, P = vox.vox_plan(s, dims, ws0, batch.status) if n else (0, 0)
+            ws = torch.empty(vox.vox_workspace_size_volume(n, dims, P), dtype=torch.uint8, device=device)
+            lst = None
+            if batch.lst is not None:
+                lst = torch.empty(max(V, 1), dtype=batch.lst.dtype, device=device)
+            mask = batch.masks[k] if batch.masks else None
+            self.items.append((s, dims, ws, lst, mask, V))
+            begin += n
+
+    def run(self, stream=None):
+        b = self.batch
+        for s, dims, ws, lst, mask, V in self.items:
+            if s.shape[0] == 0:
+                continue
+            vox.vox_generate(s, dims, ws, b.status, lst, mask, b.flags, stream, capacity=V)

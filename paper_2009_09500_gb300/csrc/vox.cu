@@ -239,13 +239,15 @@ bool uses_bricks(int64_t n, vox_dims dims, size_t ws_bytes, BrickGeom *G)
 // Count + scan. With a brick workspace it also zeroes the brick arrays and
 // counts every segment's pieces per brick (k_bin_count).
 vox_status launch_count_scan(const vox_segment *segs, int64_t n, vox_dims dims, int32_t *counts,
-                             int64_t *offsets_out, void *ws, size_t ws_bytes, int32_t *status, cudaStream_t stream)
+                             int64_t *offsets_out, void *ws, size_t ws_bytes, int32_t *status, cudaStream_t stream,
+                             const SceneDesc *scenes = nullptr, const int32_t *scene_of = nullptr,
+                             int32_t n_scenes = 0)
 {
     const WsLayout L = ws_layout(n);
     char *base = static_cast<char *>(ws);
     if (cudaMemsetAsync(base, 0, L.offsets, stream) != cudaSuccess) return VOX_ERR_CUDA;
     BrickGeom G;
-    const bool bins = uses_bricks(n, dims, ws_bytes, &G);
+    const bool bins = scene_of == nullptr && uses_bricks(n, dims, ws_bytes, &G);
     VolLayout VL{};
     if (bins) {
         VL = vol_layout(n, G, 0);
@@ -268,6 +270,9 @@ vox_status launch_count_scan(const vox_segment *segs, int64_t n, vox_dims dims, 
     p.n_tiles = L.n_tiles;
     p.stall_tile = g_stall_tile.load();
     p.wait_ns = static_cast<uint64_t>(g_wait_ns.load());
+    p.scenes = scenes;
+    p.scene_of = scene_of;
+    p.n_scenes = n_scenes;
     k_scan<true><<<static_cast<unsigned>(L.n_tiles), kScanThreads, 0, stream>>>(p);
     if (bins) {
         BinParams bp{};
@@ -299,7 +304,9 @@ vox_status launch_gen_t(const GenParams &p, cudaStream_t stream)
 
 vox_status launch_generate(const vox_segment *segs, int64_t n, vox_dims dims, void *list, int64_t capacity,
                            uint32_t *mask, int flags, void *ws, int32_t *status, cudaStream_t stream,
-                           const int64_t *gate_total = nullptr, int64_t gate_cap = 0)
+                           const int64_t *gate_total = nullptr, int64_t gate_cap = 0,
+                           const SceneDesc *scenes = nullptr, const int32_t *scene_of = nullptr,
+                           int32_t n_scenes = 0)
 {
     if (n == 0) return VOX_OK;
     const WsLayout L = ws_layout(n);
@@ -318,7 +325,12 @@ vox_status launch_generate(const vox_segment *segs, int64_t n, vox_dims dims, vo
     p.min_per_cta = kMinPerCta;
     p.gate_total = gate_total;
     p.gate_cap = gate_cap;
-    const bool lin64 = volume_bits(dims) > (uint64_t(1) << 32);
+    p.scenes = scenes;
+    p.scene_of = scene_of;
+    p.n_scenes = n_scenes;
+    p.interleave = scene_of != nullptr ? 1 : 0;
+    // batched volumes may differ in size: 64-bit bit indices cover them all
+    const bool lin64 = scene_of != nullptr || volume_bits(dims) > (uint64_t(1) << 32);
     const bool bm = flags & VOX_OUT_BITMASK;
     if (flags & VOX_OUT_LIST32) {
         return bm ? launch_gen_t<kOutList32 | kOutMask, false>(p, stream) : launch_gen_t<kOutList32, false>(p, stream);
@@ -372,6 +384,9 @@ vox_status launch_bricks(const vox_segment *segs, int64_t n, const BrickGeom &G,
     sp.n_tiles = VL.n_tiles;
     sp.stall_tile = -1;
     sp.wait_ns = static_cast<uint64_t>(g_wait_ns.load());
+    sp.scenes = nullptr;
+    sp.scene_of = nullptr;
+    sp.n_scenes = 0;
     k_scan<false><<<static_cast<unsigned>(VL.n_tiles), kScanThreads, 0, stream>>>(sp);
     if (count_only) return cudaGetLastError() == cudaSuccess ? VOX_OK : VOX_ERR_CUDA;
     k_bin_scatter<<<static_cast<unsigned>(bin_blocks), 256, 0, stream>>>(bp);
@@ -414,6 +429,28 @@ vox_status launch_outputs(const vox_segment *segs, int64_t n, vox_dims dims, voi
             return e;
     }
     return launch_bricks(segs, n, G, dims, mask, ws, ws_bytes, status, stream);
+}
+
+// ---- batched scenes ----------------------------------------------------------
+static_assert(sizeof(vox_scene) == sizeof(SceneDesc), "vox_scene and SceneDesc must match");
+static_assert(offsetof(vox_scene, dims) == offsetof(SceneDesc, w) && offsetof(vox_scene, mask) == offsetof(SceneDesc, mask),
+              "vox_scene and SceneDesc must match");
+
+// Batched workspace: the single-scene layout for all segments, then the
+// segment -> scene map and the per-scene voxel bases.
+struct BatchLayout {
+    size_t scene_of;  // int32 [n_total]
+    size_t base;      // int64 [n_scenes + 1]
+    size_t total;
+};
+
+BatchLayout batch_layout(int64_t n_total, int32_t n_scenes)
+{
+    BatchLayout B;
+    B.scene_of = ws_layout(n_total).total;
+    B.base = B.scene_of + align_up(4 * static_cast<size_t>(n_total > 0 ? n_total : 1));
+    B.total = B.base + align_up(8 * static_cast<size_t>(n_scenes + 1));
+    return B;
 }
 
 // ---- allocation-free variant: scratch in a static device array -------------
@@ -519,6 +556,64 @@ vox_status vox_generate_from_scan(const vox_segment *d_segs, int64_t n, vox_dims
         return e;
     return launch_outputs(d_segs, n, dims, d_list, list_capacity, d_mask, flags, d_ws, ws_bytes, d_status,
                           static_cast<cudaStream_t>(stream));
+}
+
+size_t vox_workspace_size_batched(int64_t n_total, int32_t n_scenes)
+{
+    if (n_total < 0 || n_scenes < 1) return 0;
+    return batch_layout(n_total, n_scenes).total;
+}
+
+vox_status vox_generate_batched(const vox_segment *d_segs, int64_t n_total, const vox_scene *d_scenes,
+                                int32_t n_scenes, void *d_list, int64_t list_capacity, int flags,
+                                int64_t *d_scene_base, void *d_ws, size_t ws_bytes, int32_t *d_status, void *stream)
+{
+    if (n_total < 0 || n_scenes < 1 || d_scenes == nullptr || d_status == nullptr) return VOX_ERR_INVALID_ARG;
+    if (n_total > 0 && d_segs == nullptr) return VOX_ERR_INVALID_ARG;
+    if (flags & ~(VOX_OUT_LIST32 | VOX_OUT_LIST64 | VOX_OUT_BITMASK)) return VOX_ERR_INVALID_ARG;
+    const bool l32 = flags & VOX_OUT_LIST32, l64 = flags & VOX_OUT_LIST64, bm = flags & VOX_OUT_BITMASK;
+    if (!(l32 || l64 || bm) || (l32 && l64)) return VOX_ERR_INVALID_ARG;
+    if ((l32 || l64) && (d_list == nullptr || list_capacity < 0)) return VOX_ERR_INVALID_ARG;
+    if (n_total > 0 && !aligned(d_segs, 16)) return VOX_ERR_ALIGNMENT;
+    if ((l32 || l64) && !aligned(d_list, 16)) return VOX_ERR_ALIGNMENT;
+    if (!aligned(d_scenes, 8)) return VOX_ERR_ALIGNMENT;
+    const BatchLayout B = batch_layout(n_total, n_scenes);
+    if (d_ws == nullptr || !aligned(d_ws, kWsAlign) || ws_bytes < B.total) return VOX_ERR_WORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char *base = static_cast<char *>(d_ws);
+    const SceneDesc *scenes = reinterpret_cast<const SceneDesc *>(d_scenes);
+    int32_t *scene_of = reinterpret_cast<int32_t *>(base + B.scene_of);
+    if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), s) != cudaSuccess) return VOX_ERR_CUDA;
+    k_scene_map<<<static_cast<unsigned>(n_scenes), 256, 0, s>>>(scenes, n_scenes, n_total, scene_of, d_status,
+                                                                 l32 ? 1 : 0);
+    if (cudaGetLastError() != cudaSuccess) return VOX_ERR_CUDA;
+    if (n_total > 0) {
+        const vox_dims unused{1, 1, 1};
+        if (vox_status e = launch_count_scan(d_segs, n_total, unused, nullptr, nullptr, d_ws, ws_bytes, d_status, s,
+                                             scenes, scene_of, n_scenes))
+            return e;
+    } else {
+        const WsLayout L = ws_layout(0);
+        if (cudaMemsetAsync(base + L.offsets, 0, 4 * sizeof(int64_t), s) != cudaSuccess) return VOX_ERR_CUDA;
+    }
+    const WsLayout L = ws_layout(n_total);
+    k_scene_base<<<static_cast<unsigned>((n_scenes + 1 + 255) / 256), 256, 0, s>>>(
+        scenes, n_scenes, reinterpret_cast<const int64_t *>(base + L.offsets), n_total,
+        reinterpret_cast<int64_t *>(base + B.base), d_scene_base, d_status);
+    if (cudaGetLastError() != cudaSuccess) return VOX_ERR_CUDA;
+    if (n_total == 0) return VOX_OK;
+    const vox_dims unused{1, 1, 1};
+    if (l32 || l64) {
+        if (vox_status e = launch_generate(d_segs, n_total, unused, d_list, list_capacity, nullptr,
+                                           flags & (VOX_OUT_LIST32 | VOX_OUT_LIST64), d_ws, d_status, s))
+            return e;
+    }
+    if (bm) {
+        if (vox_status e = launch_generate(d_segs, n_total, unused, nullptr, 0, nullptr, VOX_OUT_BITMASK, d_ws, d_status,
+                                           s, nullptr, 0, scenes, scene_of, n_scenes))
+            return e;
+    }
+    return VOX_OK;
 }
 
 size_t vox_workspace_size_volume(int64_t n, vox_dims dims, int64_t piece_capacity)

@@ -42,6 +42,16 @@ constexpr int32_t kStOutOfBounds = 2;
 constexpr int32_t kStCapacity = 4;
 constexpr int32_t kStTimeout = 5;
 
+// Device view of vox_scene (same layout): one scene of a batch.
+struct SceneDesc {
+    int64_t seg_begin;  // first segment of the scene in the batch's segment array
+    int64_t n;          // segments of the scene
+    int32_t w, h, d;    // volume extent
+    int32_t reserved;
+    uint32_t *mask;     // the scene's volume, or null
+};
+static_assert(sizeof(SceneDesc) == 40, "scene layout");
+
 struct ScanParams {
     const int32_t *segs;       // [n][6] (segment counts) or null
     const int32_t *counts_in;  // [n] (plain counts) or null
@@ -57,6 +67,9 @@ struct ScanParams {
     int64_t n_tiles;
     int64_t stall_tile;  // test hook: this tile publishes nothing (-1: off)
     uint64_t wait_ns;    // bound of every wait
+    const SceneDesc *scenes;  // batched: per-segment dims come from the segment's scene
+    const int32_t *scene_of;  // batched: scene index of every segment (else null)
+    int32_t n_scenes;
 };
 
 // ---------------------------------------------------------------- count + scan
@@ -94,9 +107,19 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(ScanParams p)
             const int2 *r = reinterpret_cast<const int2 *>(p.segs + 6 * s);
             const int2 a = __ldg(r), b = __ldg(r + 1), e = __ldg(r + 2);
             const int32_t x0 = a.x, y0 = a.y, z0 = b.x, x1 = b.y, y1 = e.x, z1 = e.y;
-            const bool ok = (unsigned)x0 < (unsigned)p.w && (unsigned)x1 < (unsigned)p.w &&
-                            (unsigned)y0 < (unsigned)p.h && (unsigned)y1 < (unsigned)p.h &&
-                            (unsigned)z0 < (unsigned)p.d && (unsigned)z1 < (unsigned)p.d;
+            int32_t W = p.w, H = p.h, D = p.d;
+            if (p.scene_of != nullptr) {  // batched: the segment's own scene
+                const int32_t k = __ldg(p.scene_of + s);
+                W = H = D = 0;  // an unmapped segment fails the bounds check
+                if ((unsigned)k < (unsigned)p.n_scenes) {
+                    W = p.scenes[k].w;
+                    H = p.scenes[k].h;
+                    D = p.scenes[k].d;
+                }
+            }
+            const bool ok = (unsigned)x0 < (unsigned)W && (unsigned)x1 < (unsigned)W &&
+                            (unsigned)y0 < (unsigned)H && (unsigned)y1 < (unsigned)H &&
+                            (unsigned)z0 < (unsigned)D && (unsigned)z1 < (unsigned)D;
             if (ok) {
                 c = max(abs(x1 - x0), max(abs(y1 - y0), abs(z1 - z0))) + 1;
             } else {
@@ -231,6 +254,10 @@ struct GenParams {
     int64_t min_per_cta;     // smallest voxel range worth a CTA (multiple of 4)
     const int64_t *gate_total;  // if set, run only when *gate_total > gate_cap
     int64_t gate_cap;
+    const SceneDesc *scenes;    // batched volume: per-segment volume from its scene
+    const int32_t *scene_of;    // (else null: one volume, p.w / p.h / p.mask)
+    int32_t n_scenes;
+    int32_t interleave;         // voxel tiles dealt round-robin to CTAs (else one range per CTA)
 };
 
 // Shared memory of k_generate: the staged window of segments and, for list
@@ -308,7 +335,7 @@ __device__ __forceinline__ void red_or_keep(uint32_t *addr, uint32_t bits, uint6
 }
 
 template <int R, int OUT, bool LIN64>
-__global__ void __launch_bounds__(kGenThreads) k_generate(GenParams p)
+__global__ void __launch_bounds__(kGenThreads, 3) k_generate(GenParams p)
 {
     using L = GenLayout<R, OUT>;
     using PackT = typename std::conditional<L::kWide, uint64_t, uint32_t>::type;
@@ -340,22 +367,36 @@ __global__ void __launch_bounds__(kGenThreads) k_generate(GenParams p)
     __syncthreads();
     if (!sm.go) return;
     const int64_t V = sm.V;
-    // contiguous voxel range of this CTA, a multiple of 4 long
+    // voxel ranges: one contiguous range per CTA (a multiple of 4 long), or
+    // tiles of one pass dealt round-robin, so that the CTAs sweep the voxel
+    // order together (the volumes they touch at any moment stay few and hot)
     int64_t per = (V + gridDim.x - 1) / gridDim.x;
     per = max(per, p.min_per_cta);
     per = (per + 3) & ~int64_t(3);
-    const int64_t gA = static_cast<int64_t>(blockIdx.x) * per;
-    if (gA >= V) return;
-    const int64_t gB = min64(gA + per, V);
+    if (p.interleave) per = kPass;
 
     uint64_t keep_policy = 0;
     if (kMask) asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep_policy));
     uint32_t phase = 0;
-    int64_t s_cur = find_segment_block(p.offsets, 0, p.n, gA);
 
-    const LinT w = static_cast<LinT>(p.w);
-    const LinT wh = static_cast<LinT>(p.w) * static_cast<LinT>(p.h);
+    LinT w = static_cast<LinT>(p.w);
+    LinT wh = static_cast<LinT>(p.w) * static_cast<LinT>(p.h);
+    uint32_t *mask_s = p.mask;
+    const bool batched = p.scene_of != nullptr;
+    // the volume of segment `seg` (batched): dims and base pointer of its scene
+#define VOX_USE_SCENE_OF(seg)                                              \
+    do {                                                                   \
+        const SceneDesc &sd_ = p.scenes[__ldg(p.scene_of + (seg))];        \
+        w = static_cast<LinT>(sd_.w);                                      \
+        wh = static_cast<LinT>(sd_.w) * static_cast<LinT>(sd_.h);          \
+        mask_s = sd_.mask;                                                 \
+    } while (0)
     PackT *const list = static_cast<PackT *>(p.list);
+    for (int64_t range = blockIdx.x;; range += gridDim.x) {
+    const int64_t gA = range * per;
+    if (gA >= V) break;
+    const int64_t gB = min64(gA + per, V);
+    int64_t s_cur = find_segment_block(p.offsets, 0, p.n, gA);
     int64_t g0 = gA;
     while (g0 < gB) {
         // ---- stage a window of segment records and offsets (TMA bulk copies)
@@ -393,6 +434,7 @@ __global__ void __launch_bounds__(kGenThreads) k_generate(GenParams p)
             if (g < g_end) {
                 const int32_t len = static_cast<int32_t>(min64(R, g_end - g));
                 int32_t j = find_in_window(sm.offs, cnt, g);
+                if (kMask && batched) VOX_USE_SCENE_OF(s_base + j);
                 Stepper<PackT, LinT> st;
                 st.enter(sm.recs + 6 * j, static_cast<int32_t>(g - sm.offs[j]), w, wh);
                 uint32_t *sp = sm.stage + t;
@@ -411,7 +453,7 @@ __global__ void __launch_bounds__(kGenThreads) k_generate(GenParams p)
                         if (kMask) {
                             const LinT word = st.L >> 5;
                             if (word != cur_word) {
-                                if (acc) red_or_keep(p.mask + cur_word, acc, keep_policy);
+                                if (acc && mask_s) red_or_keep(mask_s + cur_word, acc, keep_policy);
                                 cur_word = word;
                                 acc = 0;
                             }
@@ -422,9 +464,15 @@ __global__ void __launch_bounds__(kGenThreads) k_generate(GenParams p)
                     u += m;
                     if (u >= len) break;
                     ++j;  // the run continues in the next segment of the window
+                    if (kMask && batched) {  // the next segment may live in another volume
+                        if (acc && mask_s) red_or_keep(mask_s + cur_word, acc, keep_policy);
+                        acc = 0;
+                        cur_word = static_cast<LinT>(~LinT(0));
+                        VOX_USE_SCENE_OF(s_base + j);
+                    }
                     st.enter(sm.recs + 6 * j, 0, w, wh);
                 }
-                if (kMask && acc) red_or_keep(p.mask + cur_word, acc, keep_policy);
+                if (kMask && acc && mask_s) red_or_keep(mask_s + cur_word, acc, keep_policy);  // scenes may have no volume
             }
             if (kList) {
                 // ---- write the pass out: four consecutive voxels per thread, 16-byte stores
@@ -465,6 +513,42 @@ __global__ void __launch_bounds__(kGenThreads) k_generate(GenParams p)
         g0 = g_end;
         if (g0 < gB) s_cur = (g0 >= win_end) ? s_base + cnt : s_base + find_in_window(sm.offs, cnt, g0);
     }
+    if (!p.interleave) break;
+    }
+#undef VOX_USE_SCENE_OF
+}
+
+// Batched scenes: check the scene table (contiguous, in order, covering all n
+// segments; dims in range; 32-bit lists need edges <= 1024) and record each
+// segment's scene. One CTA per scene. Any error goes to *status and the
+// generation kernels then write nothing.
+__global__ void __launch_bounds__(256) k_scene_map(const SceneDesc *scenes, int32_t n_scenes, int64_t n_total,
+                                                   int32_t *scene_of, int32_t *status, int32_t list32)
+{
+    const int32_t k = blockIdx.x;
+    const SceneDesc sd = scenes[k];
+    const int64_t expect = k == 0 ? 0 : scenes[k - 1].seg_begin + scenes[k - 1].n;
+    const int32_t lim = 1 << 21;
+    bool ok = sd.n >= 0 && sd.seg_begin == expect && sd.seg_begin + sd.n <= n_total && sd.reserved == 0 &&
+              sd.w >= 1 && sd.h >= 1 && sd.d >= 1 && sd.w <= lim && sd.h <= lim && sd.d <= lim;
+    if (k == n_scenes - 1) ok = ok && sd.seg_begin + sd.n == n_total;
+    if (threadIdx.x == 0) {
+        if (!ok) set_status(status, 1);  // VOX_ERR_INVALID_ARG
+        else if (list32 && (sd.w > 1024 || sd.h > 1024 || sd.d > 1024)) set_status(status, 3);  // PACK_WIDTH
+    }
+    if (!ok) return;
+    for (int64_t i = threadIdx.x; i < sd.n; i += blockDim.x) scene_of[sd.seg_begin + i] = k;
+}
+
+// First global voxel id of every scene (and V at index n_scenes).
+__global__ void k_scene_base(const SceneDesc *scenes, int32_t n_scenes, const int64_t *offsets, int64_t n_total,
+                             int64_t *base, int64_t *base_out, const int32_t *status)
+{
+    const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (k > n_scenes || ld_volatile_i32(status) != 0) return;
+    const int64_t v = k < n_scenes ? __ldg(offsets + scenes[k].seg_begin) : __ldg(offsets + n_total);
+    base[k] = v;
+    if (base_out) base_out[k] = v;
 }
 
 }  // namespace vox

@@ -37,7 +37,7 @@ EXPORTED = (
     "vox_workspace_size", "vox_count", "vox_generate", "vox_generate_from_scan",
     "vox_host_arena_size", "vox_generate_host", "vox_strerror", "vox_mask_words",
     "vox_debug_set_scan_stall", "vox_scan_tile_segments", "vox_generate_noalloc",
-    "vox_workspace_size_volume", "vox_plan",
+    "vox_workspace_size_volume", "vox_plan", "vox_workspace_size_batched", "vox_generate_batched",
 )
 NOALLOC_MAX_SEGMENTS = 2000000
 
@@ -97,6 +97,10 @@ def load(path: str | None = None):
     lib.vox_workspace_size_volume.restype = sz
     lib.vox_plan.argtypes = [vp, i64, Dims, vp, sz, vp, vp, vp, vp]
     lib.vox_plan.restype = i32
+    lib.vox_workspace_size_batched.argtypes = [i64, ctypes.c_int32]
+    lib.vox_workspace_size_batched.restype = sz
+    lib.vox_generate_batched.argtypes = [vp, i64, vp, ctypes.c_int32, vp, i64, i32, vp, vp, sz, vp, vp]
+    lib.vox_generate_batched.restype = i32
     lib.vox_generate_noalloc.argtypes = [vp, i64, Dims, vp, i64, vp, i32, vp, vp]
     lib.vox_generate_noalloc.restype = i32
     if path == _build.LIB:
@@ -150,6 +154,10 @@ def vox_plan(segs, dims, ws, status, stream=None):
                          _ptr(status), ctypes.byref(V), ctypes.byref(P), _stream(stream))
     _check(st, "vox_plan")
     return int(V.value), int(P.value)
+
+
+def vox_workspace_size_batched(n_total: int, n_scenes: int) -> int:
+    return int(load().vox_workspace_size_batched(int(n_total), int(n_scenes)))
 
 
 def vox_mask_words(dims) -> int:

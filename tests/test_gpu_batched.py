@@ -1,0 +1,138 @@
+"""Batched scenes through vox_generate_batched, against the oracle scene by
+scene, against per-scene plain launches, and replayed from a CUDA graph
+(bit-exact everywhere: integer outputs)."""
+
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import get_oracle
+from paper_2009_09500_gb300 import batching, vox, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2009_09500_gb300 import build
+
+    build.build_library()
+    vox.load()
+
+
+def check_scenes(batch, scenes, sample=None):
+    O = get_oracle()
+    torch.cuda.synchronize()
+    assert int(batch.status.item()) == 0, vox.strerror(int(batch.status.item()))
+    base = batch.scene_base.cpu().numpy()
+    counts = np.concatenate([O.count(w.segs) for w in scenes]).astype(np.int64)
+    per_scene = np.array([O.total(w.segs) for w in scenes])
+    assert np.array_equal(np.diff(base), per_scene)
+    assert base[-1] == counts.sum() == batch.V
+    lst = batch.lst.cpu().numpy() if batch.lst is not None else None
+    ks = range(len(scenes)) if sample is None else sample
+    for k in ks:
+        w = scenes[k]
+        if lst is not None:
+            got = lst[base[k]:base[k + 1]]
+            want = O.list64(w.segs) if batch.flags & vox.OUT_LIST64 else O.list32(w.segs)
+            assert np.array_equal(got.view(want.dtype), want), f"scene {k} list"
+        if batch.masks:
+            got = batch.masks[k].cpu().numpy().view(np.uint32)
+            assert np.array_equal(got, O.bitmask(w.segs, w.dims)), f"scene {k} volume"
+
+
+def small_scenes(n=24, seed=40):
+    return workloads.config4(seed=seed, n_scenes=n, s_lo=50, s_hi=3000)
+
+
+def test_batched_small_list32_and_volumes():
+    scenes = small_scenes()
+    b = batching.make_batch(scenes)
+    b.run()
+    check_scenes(b, scenes)
+
+
+def test_batched_list64_only_and_volume_only():
+    scenes = small_scenes(12, seed=41)
+    b = batching.make_batch(scenes, flags=vox.OUT_LIST64)
+    b.run()
+    check_scenes(b, scenes)
+    b = batching.make_batch(scenes, flags=vox.OUT_BITMASK)
+    b.run()
+    check_scenes(b, scenes)
+
+
+def test_batched_with_empty_and_odd_scenes():
+    rng = np.random.default_rng(42)
+    scenes = []
+    for k, dims in enumerate([(64, 64, 64), (13, 7, 5), (96, 40, 17), (32, 32, 32), (128, 8, 300)]):
+        n = [0, 500, 1, 2049, 333][k]
+        scenes.append(workloads.Workload(f"s{k}", workloads.uniform_segments(rng, n, dims), dims))
+    b = batching.make_batch(scenes)
+    b.run()
+    check_scenes(b, scenes)
+
+
+def test_batched_config4_full_size_sampled():
+    """The 256-scene batch: scene bases in full, 24 scenes compared in full."""
+    scenes = workloads.config4()
+    b = batching.make_batch(scenes)
+    b.run()
+    rng = np.random.default_rng(7)
+    sample = sorted(set([0, len(scenes) - 1] + list(rng.choice(len(scenes), 22, replace=False))))
+    check_scenes(b, scenes, sample)
+
+
+def test_batched_equals_plain_and_graph_replay():
+    scenes = small_scenes(32, seed=43)
+    b = batching.make_batch(scenes)
+    b.run()
+    torch.cuda.synchronize()
+    ref_list = b.lst.cpu().numpy().copy()
+    ref_masks = [m.cpu().numpy().copy() for m in b.masks]
+    # plain per-scene launches into fresh volumes
+    b.clear_volumes()
+    plain = batching.PlainScenes(b)
+    plain.run()
+    torch.cuda.synchronize()
+    base = b.scene_base.cpu().numpy()
+    for k, (s, dims, ws, lst, mask, V) in enumerate(plain.items):
+        assert np.array_equal(lst[:V].cpu().numpy(), ref_list[base[k]:base[k + 1]])
+        assert np.array_equal(mask.cpu().numpy(), ref_masks[k])
+    # captured once, replayed twice into cleared volumes
+    g = batching.GraphRunner(b.run)
+    for _ in range(2):
+        b.clear_volumes()
+        b.lst.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert int(b.status.item()) == 0
+        assert np.array_equal(b.lst.cpu().numpy(), ref_list)
+        for k, m in enumerate(b.masks):
+            assert np.array_equal(m.cpu().numpy(), ref_masks[k])
+
+
+def test_batched_bad_scene_table_writes_nothing():
+    scenes = small_scenes(4, seed=44)
+    b = batching.make_batch(scenes)
+    table = bytearray(b.scenes.cpu().numpy().tobytes())
+    rec = batching.SceneRecord.from_buffer(table, 2 * 40)
+    rec.seg_begin += 1  # a gap between scene 1 and scene 2
+    b.scenes.copy_(torch.frombuffer(table, dtype=torch.uint8))
+    b.lst.fill_(-7)
+    b.run()
+    torch.cuda.synchronize()
+    assert int(b.status.item()) == vox.ERR_INVALID_ARG
+    assert (b.lst.cpu().numpy() == -7).all()
+    assert all(int(m.abs().sum().item()) == 0 for m in b.masks)
+
+
+def test_batched_list32_rejects_wide_scene():
+    rng = np.random.default_rng(45)
+    dims = (2048, 8, 8)
+    scenes = [workloads.Workload("wide", workloads.uniform_segments(rng, 100, dims), dims)]
+    b = batching.make_batch(scenes, flags=vox.OUT_LIST32)
+    b.run()
+    torch.cuda.synchronize()
+    assert int(b.status.item()) == vox.ERR_PACK_WIDTH
