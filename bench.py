@@ -201,6 +201,58 @@ def run_reference(args):
     return 0
 
 
+def measure_batched(steps: int, dev) -> dict:
+    """Batched vs plain launches on the 256-scene workload (uneven scenes, volume
+    edges 64..512, 1e3..1e5 segments each; list32 + one volume per scene):
+    one vox_generate_batched sequence (eager and replayed from a CUDA graph)
+    against one vox_generate per scene (eager and in a graph). L2 is flushed
+    between steps, outside the events."""
+    import torch
+
+    from paper_2009_09500_gb300 import batching, workloads
+
+    scenes = workloads.config4()
+    b = batching.make_batch(scenes, device=dev)
+    plain = batching.PlainScenes(b, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        ts = []
+        for i in range(reps + 2):
+            flush.zero_()
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            e.record(stream)
+            torch.cuda.synchronize()
+            if i >= 2:
+                ts.append(a.elapsed_time(e))
+        return float(np.mean(ts)), float(np.percentile(ts, 99))
+
+    reps = max(3, min(steps, 20))
+    batched_eager = timed(lambda: b.run(stream), reps)
+    plain_eager = timed(lambda: plain.run(stream), reps)
+    g_b = batching.GraphRunner(b.run)
+    batched_graph = timed(g_b.replay, reps)
+    g_p = batching.GraphRunner(plain.run)
+    plain_graph = timed(g_p.replay, reps)
+    torch.cuda.synchronize()
+    st = int(b.status.item())
+    if st != 0:
+        raise RuntimeError(f"device status {st}")
+    V = b.V
+    return {
+        "workload": "256 uneven scenes: edges {64,128,256,512}, 1e3..1e5 segments each, list32 + volume per scene",
+        "scenes": b.n_scenes, "segments": int(b.segs.shape[0]), "voxels": V,
+        "batched_graph_ms": batched_graph[0], "batched_graph_p99_ms": batched_graph[1],
+        "batched_eager_ms": batched_eager[0], "plain_eager_ms": plain_eager[0], "plain_graph_ms": plain_graph[0],
+        "voxels_per_s_batched": V / batched_graph[0] * 1e3, "voxels_per_s_plain": V / plain_eager[0] * 1e3,
+        "batched_over_plain": plain_eager[0] / batched_graph[0],
+        "launches": {"batched": 6, "plain": "up to 9 per scene (2 memsets + 7 kernels)"},
+    }
+
+
 def run_ours(args):
     import torch
 
@@ -334,6 +386,10 @@ def run_ours(args):
                        f"{reps} synchronous calls"}
         del arena
 
+    batched = None
+    if not args.no_batched and world == 1:
+        batched = measure_batched(args.steps, dev)
+
     if rank != 0:
         return 0
     cpu = None
@@ -353,6 +409,7 @@ def run_ours(args):
         "kernels_ms": {"count_scan": float(np.mean(scan_ms)), "list": list_mean, "volume": vol_mean},
         "wall_s_timed_region": wall,
         "roofline": roofline, "roofline_other": roofline_other, "cpu_baseline": cpu, "e2e": e2e,
+        "batched_vs_plain": batched,
         "clocks": clocks,
         "gpu_launches": 7 * args.steps,
         "gpu_launches_note": "per step: k_scan<true>, k_generate (list), k_bin_count, k_scan<false>, "
@@ -372,6 +429,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
     if args.warmup < 3:
