@@ -253,6 +253,33 @@ def measure_batched(steps: int, dev) -> dict:
     }
 
 
+def measure_serving(duration_s: float, dev) -> dict:
+    """The request stream: Poisson arrivals at 2000 req/s for `duration_s`,
+    each request a scene of log-uniform 1e3..1e6 segments in a 128^3..1024^3
+    volume, served by the continuous-batching loop into device-resident volumes.
+    Latency = completion (host clock, event polled) - arrival."""
+    import torch
+
+    from paper_2009_09500_gb300 import serving, workloads
+
+    stream = workloads.config5(duration_s=duration_s)
+    reqs = serving.make_requests(stream, pool_size=128)
+    free, _ = torch.cuda.mem_get_info(dev)
+    budget = int(min(64 << 30, 0.5 * free))
+    launcher = serving.GpuLauncher(slots=4, device=dev)
+    warm = serving.make_requests(workloads.config5(seed=99, duration_s=0.01), pool_size=8)
+    serving.Server(launcher, budget_bytes=budget, max_inflight=4).run(warm)
+    torch.cuda.synchronize()
+    srv = serving.Server(launcher, budget_bytes=budget, max_inflight=4, max_batch_requests=64)
+    st = srv.run(reqs)
+    out = st.summary()
+    out.update({"workload": "Poisson 2000 req/s, scenes of log-uniform 1e3..1e6 segments, edges "
+                            "{128,256,512,1024}, device-resident volumes (payloads from a pool of 128)",
+                "duration_s": duration_s, "requests": len(reqs), "budget_bytes": budget, "slots": 4,
+                "offered_voxels_per_s": sum(r.voxels for r in reqs) / duration_s})
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -389,6 +416,9 @@ def run_ours(args):
     batched = None
     if not args.no_batched and world == 1:
         batched = measure_batched(args.steps, dev)
+    served = None
+    if not args.no_serve and world == 1:
+        served = measure_serving(args.serve_seconds, dev)
 
     if rank != 0:
         return 0
@@ -409,7 +439,7 @@ def run_ours(args):
         "kernels_ms": {"count_scan": float(np.mean(scan_ms)), "list": list_mean, "volume": vol_mean},
         "wall_s_timed_region": wall,
         "roofline": roofline, "roofline_other": roofline_other, "cpu_baseline": cpu, "e2e": e2e,
-        "batched_vs_plain": batched,
+        "batched_vs_plain": batched, "serving": served,
         "clocks": clocks,
         "gpu_launches": 7 * args.steps,
         "gpu_launches_note": "per step: k_scan<true>, k_generate (list), k_bin_count, k_scan<false>, "
@@ -430,6 +460,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
     if args.warmup < 3:

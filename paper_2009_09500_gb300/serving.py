@@ -1,0 +1,280 @@
+"""Continuous-batching request loop for voxelization requests.
+
+Each request is a scene (segments + volume extent) whose result is an occupancy
+volume kept resident on the device. Requests arrive over time (a Poisson stream
+in the benchmark); the loop admits them first-come first-served while their
+device bytes fit a memory budget and an in-flight slot is free, packs the
+admitted requests into one batch, and launches the batch with
+vox_generate_batched on one of several streams. Batches launched while earlier
+ones still run overlap on the device, and requests that arrive meanwhile join
+the next batch as slots and memory free up (continuous batching). Latency is
+completion minus arrival, on the host clock.
+
+The scheduler (admission, slots, bookkeeping) is plain Python and takes its
+launcher, memory probe and clock as arguments, so that it can be exercised on
+the CPU with fakes; the default launcher runs libvox on the GPU.
+"""
+
+from __future__ import annotations
+
+import collections
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class ServeRequest:
+    rid: int
+    arrival_s: float
+    n: int
+    dims: tuple
+    segs_host: object = None      # pinned CPU int32 [n, 6] tensor (default launcher)
+    voxels: int = 0               # total voxels (for throughput accounting)
+    admitted_s: float = math.nan
+    done_s: float = math.nan
+    status: int = -1
+    batch_id: int = -1
+    result: object = None         # the resident volume (device int32 tensor), if kept
+
+    @property
+    def mask_bytes(self) -> int:
+        w, h, d = self.dims
+        return 4 * ((w * h * d + 31) // 32)
+
+    @property
+    def device_bytes(self) -> int:
+        """Volume + segments + workspace share of this request on the device."""
+        return self.mask_bytes + 24 * self.n + 16 * self.n + 256
+
+    @property
+    def latency_ms(self) -> float:
+        return 1000.0 * (self.done_s - self.arrival_s)
+
+
+class Admission:
+    """First-come first-served admission: take requests from the head of the
+    queue while they fit the free-byte budget and the batch limits; a request
+    larger than the whole budget can never run and is rejected."""
+
+    def __init__(self, budget_bytes: int, max_batch_requests: int = 64, max_batch_segments: int = 1 << 24):
+        self.budget_bytes = int(budget_bytes)
+        self.max_batch_requests = int(max_batch_requests)
+        self.max_batch_segments = int(max_batch_segments)
+
+    def take(self, queue: collections.deque, bytes_in_use: int):
+        batch, rejected = [], []
+        used = bytes_in_use
+        segs = 0
+        while queue and len(batch) < self.max_batch_requests:
+            r = queue[0]
+            if r.device_bytes > self.budget_bytes:
+                rejected.append(queue.popleft())
+                continue
+            if used + r.device_bytes > self.budget_bytes or (batch and segs + r.n > self.max_batch_segments):
+                break  # head of line waits for memory (keeps arrival order)
+            batch.append(queue.popleft())
+            used += r.device_bytes
+            segs += r.n
+        return batch, rejected
+
+
+@dataclass
+class InFlight:
+    bid: int
+    reqs: list
+    handle: object      # launcher's handle (completion test + buffers kept alive)
+    bytes: int
+    slot: int
+    launched_s: float
+
+
+@dataclass
+class ServeStats:
+    completed: int = 0
+    rejected: int = 0
+    failed: int = 0
+    batches: int = 0
+    voxels: int = 0
+    wall_s: float = 0.0
+    max_bytes_in_use: int = 0
+    max_inflight: int = 0
+    latencies_ms: list = field(default_factory=list)
+
+    def summary(self) -> dict:
+        lat = np.array(self.latencies_ms) if self.latencies_ms else np.array([math.nan])
+        return {
+            "completed": self.completed, "rejected": self.rejected, "failed": self.failed,
+            "batches": self.batches, "mean_batch": self.completed / max(1, self.batches),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(np.mean(lat)), "voxels": self.voxels,
+            "voxels_per_s": self.voxels / self.wall_s if self.wall_s > 0 else 0.0,
+            "wall_s": self.wall_s, "max_bytes_in_use": self.max_bytes_in_use, "max_inflight": self.max_inflight,
+        }
+
+
+class Server:
+    """The request loop. ``launcher(reqs, slot) -> handle`` starts a batch;
+    ``handle.done() -> bool`` polls it; ``handle.finish() -> status`` collects it
+    (and may attach results to the requests)."""
+
+    def __init__(self, launcher, budget_bytes: int, max_inflight: int = 4, max_batch_requests: int = 64,
+                 max_batch_segments: int = 1 << 24, clock=time.perf_counter, idle_sleep_s: float = 20e-6):
+        self.launcher = launcher
+        self.admission = Admission(budget_bytes, max_batch_requests, max_batch_segments)
+        self.max_inflight = int(max_inflight)
+        self.clock = clock
+        self.idle_sleep_s = idle_sleep_s
+
+    def run(self, requests, time_limit_s: float = 600.0) -> ServeStats:
+        pending = collections.deque(sorted(requests, key=lambda r: r.arrival_s))
+        queue = collections.deque()
+        inflight = []
+        free_slots = list(range(self.max_inflight))
+        stats = ServeStats()
+        bytes_in_use = 0
+        bid = 0
+        t0 = self.clock()
+        first_arrival = pending[0].arrival_s if pending else 0.0
+        last_done = first_arrival
+        while pending or queue or inflight:
+            now = self.clock() - t0
+            if now > time_limit_s:
+                raise TimeoutError("serving loop exceeded its time limit")
+            progressed = False
+            while pending and pending[0].arrival_s <= now:
+                queue.append(pending.popleft())
+                progressed = True
+            # completions
+            for b in list(inflight):
+                if b.handle.done():
+                    st = b.handle.finish()
+                    t = self.clock() - t0
+                    for r in b.reqs:
+                        r.done_s = t
+                        r.status = st
+                        if st == 0:
+                            stats.completed += 1
+                            stats.voxels += r.voxels
+                            stats.latencies_ms.append(r.latency_ms)
+                        else:
+                            stats.failed += 1
+                    last_done = max(last_done, t)
+                    bytes_in_use -= b.bytes
+                    free_slots.append(b.slot)
+                    inflight.remove(b)
+                    progressed = True
+            # admission + launch (continuous batching)
+            if queue and free_slots:
+                batch, rejected = self.admission.take(queue, bytes_in_use)
+                for r in rejected:
+                    r.status = -2
+                    stats.rejected += 1
+                if batch:
+                    slot = free_slots.pop(0)
+                    t = self.clock() - t0
+                    for r in batch:
+                        r.admitted_s = t
+                        r.batch_id = bid
+                    nbytes = sum(r.device_bytes for r in batch)
+                    handle = self.launcher(batch, slot)
+                    inflight.append(InFlight(bid, batch, handle, nbytes, slot, t))
+                    bytes_in_use += nbytes
+                    stats.batches += 1
+                    stats.max_bytes_in_use = max(stats.max_bytes_in_use, bytes_in_use)
+                    stats.max_inflight = max(stats.max_inflight, len(inflight))
+                    bid += 1
+                    progressed = True
+            if not progressed and self.idle_sleep_s > 0:
+                time.sleep(self.idle_sleep_s)
+        stats.wall_s = max(1e-9, last_done - first_arrival)
+        return stats
+
+
+# ------------------------------------------------------------- GPU launcher
+class _Handle:
+    def __init__(self, event, keep, reqs, keep_results):
+        self.event = event
+        self.keep = keep
+        self.reqs = reqs
+        self.keep_results = keep_results
+
+    def done(self) -> bool:
+        return self.event.query()
+
+    def finish(self) -> int:
+        status = int(self.keep["status"].item())
+        if self.keep_results and status == 0:
+            for r, m in zip(self.reqs, self.keep["masks"]):
+                r.result = m
+        self.keep = None
+        return status
+
+
+class GpuLauncher:
+    """Launches a batch with vox_generate_batched (volumes only) on one of
+    ``slots`` streams: segments copied from pinned host memory, fresh zeroed
+    volumes, one scene table, one workspace, one completion event."""
+
+    def __init__(self, slots: int, device="cuda", keep_results: bool = False):
+        import torch
+
+        self.device = torch.device(device)
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
+        self.keep_results = keep_results
+
+    def __call__(self, reqs, slot):
+        import torch
+
+        from . import batching, vox
+
+        stream = self.streams[slot]
+        n_total = sum(r.n for r in reqs)
+        with torch.cuda.stream(stream):
+            segs = torch.empty((max(n_total, 1), 6), dtype=torch.int32, device=self.device)
+            off = 0
+            for r in reqs:
+                if r.n:
+                    segs[off:off + r.n].copy_(r.segs_host, non_blocking=True)
+                off += r.n
+            masks = [torch.zeros((r.mask_bytes // 4,), dtype=torch.int32, device=self.device) for r in reqs]
+            table = batching.scene_table_bytes([r.n for r in reqs], [r.dims for r in reqs],
+                                               [m.data_ptr() for m in masks])
+            scenes = torch.frombuffer(bytearray(table), dtype=torch.uint8).pin_memory().to(self.device,
+                                                                                         non_blocking=True)
+            ws = torch.empty(vox.vox_workspace_size_batched(n_total, len(reqs)), dtype=torch.uint8,
+                             device=self.device)
+            status = torch.zeros(1, dtype=torch.int32, device=self.device)
+            st = vox.load().vox_generate_batched(
+                vox._ptr(segs), n_total, vox._ptr(scenes), len(reqs), None, 0, vox.OUT_BITMASK, None,
+                vox._ptr(ws), ws.numel(), vox._ptr(status), vox._stream(stream))
+            if st != vox.OK:
+                raise vox.VoxError(st, "vox_generate_batched")
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        keep = {"segs": segs, "masks": masks, "scenes": scenes, "ws": ws, "status": status}
+        return _Handle(ev, keep, reqs, self.keep_results)
+
+
+def make_requests(stream_reqs, pool_size: int = 256, seed: int = 11):
+    """Turn a workloads.config5 arrival stream into ServeRequests with pinned
+    host payloads. Payloads come from a pool of `pool_size` scenes drawn with the
+    stream's own sizes (request i carries pool[i % pool_size]), so that a long
+    stream does not need one fresh host buffer per request."""
+    import torch
+
+    pool = {}
+    out = []
+    for i, rq in enumerate(stream_reqs):
+        key = i % pool_size
+        if key not in pool:
+            w = rq.workload()
+            segs = torch.from_numpy(w.segs).pin_memory()
+            d = np.abs(w.segs[:, 3:].astype(np.int64) - w.segs[:, :3])
+            pool[key] = (segs, tuple(w.dims), int((d.max(axis=1) + 1).sum()) if w.n else 0)
+        segs, dims, voxels = pool[key]
+        out.append(ServeRequest(rid=i, arrival_s=rq.arrival_s, n=int(segs.shape[0]), dims=dims, segs_host=segs,
+                                voxels=voxels))
+    return out
