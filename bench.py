@@ -201,6 +201,25 @@ def run_reference(args):
     return 0
 
 
+def aggregate_ranks(ms_local: float, voxels_local: int, world: int, device):
+    """Whole-job figures over the ranks: the slowest rank's mean step time, the
+    voxels of all ranks, and value = all voxels / slowest time (weak scaling:
+    every rank voxelizes its own batch; no data crosses ranks)."""
+    import torch
+
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        v = torch.tensor([voxels_local], dtype=torch.int64, device=device)
+        dist.all_reduce(v, op=dist.ReduceOp.SUM)
+        ms_max, total = float(t.item()), int(v.item())
+    else:
+        ms_max, total = float(ms_local), int(voxels_local)
+    return ms_max, total, total / (ms_max / 1000.0)
+
+
 def measure_batched(steps: int, dev) -> dict:
     """Batched vs plain launches on the 256-scene workload (uneven scenes, volume
     edges 64..512, 1e3..1e5 segments each; list32 + one volume per scene):
@@ -360,14 +379,7 @@ def run_ours(args):
     list_ms = [e[1].elapsed_time(e[2]) for e in evs]
     vol_ms = [e[2].elapsed_time(e[3]) for e in evs]
     ms_mean = float(np.mean(step_ms))
-    if world > 1:
-        t = torch.tensor([ms_mean], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_mean_max = float(t.item())
-    else:
-        ms_mean_max = ms_mean
-    total_voxels = V * world
-    value = total_voxels / (ms_mean_max / 1000.0)
+    ms_mean_max, total_voxels, value = aggregate_ranks(ms_mean, V, world, dev)
 
     # rooflines: algorithmic bytes per launch / mean duration from the step's events
     peaks, peak_kind = _measured_peaks()
