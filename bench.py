@@ -331,6 +331,12 @@ def run_ours(args):
     mask = torch.zeros(words, dtype=torch.int32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     flags = vox.OUT_LIST32 | vox.OUT_BITMASK
+    tuning = None
+    if not args.no_tune:  # launch tuning for this GPU and workload class (outputs do not depend on it)
+        from paper_2009_09500_gb300 import autotune
+
+        tuning = autotune.get_or_tune(lambda: vox.vox_generate(segs, w.dims, ws, status, lst, mask, flags),
+                                      n, V, w.dims, flags, reps=3)
 
     # one step = the launches of vox_generate(list32 | volume), issued as its three
     # phases so that each phase gets its own events: count + scan, list, volume
@@ -394,8 +400,10 @@ def run_ours(args):
                  "bytes_model": "24 B/segment read + 4 B/voxel written"}
     roof_vol = {"bound": "hbm", "achieved": vol_bytes / vol_mean / 1e6, "peak": hbm, "unit": "GB/s",
                 "frac": vol_bytes / vol_mean / 1e6 / hbm, "traffic": _recorded_traffic("k_brick_volume"),
-                "kernel": "volume phase: k_bin_count + k_scan<false> + k_bin_scatter + k_brick_volume "
-                          "(+ gated atomic fallback, exits at once)",
+                "kernel": ("volume phase: k_generate<volume> (per-voxel atomics)"
+                           if tuning and tuning["params"]["volume_path"] == 1 else
+                           "volume phase: k_scan<false> + k_bin_scatter + k_brick_volume "
+                           "(+ gated atomic fallback, exits at once; k_bin_count runs in the count phase)"),
                 "peak_kind": f"{peak_kind} HBM copy", "algorithmic_bytes_per_launch": vol_bytes, "ms": vol_mean,
                 "bytes_model": "24 B/segment read + 64 B per distinct 32-B volume sector (read + write)",
                 "pieces": P}
@@ -442,7 +450,10 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_mean_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "segments": n, "voxels_per_gpu": V, "volume": list(w.dims),
-                   "outputs": "list32 + bitmask", "volume_path": "brick ownership", "pieces": P,
+                   "outputs": "list32 + bitmask",
+                   "volume_path": "per-voxel atomics" if tuning and tuning["params"]["volume_path"] == 1
+                   else "brick ownership", "pieces": P,
+                   "tuning": tuning,
                    "launch": "plain (count+scan, list, volume) on one stream",
                    "l2": "flushed between steps by a 256 MiB write (outside the step events)",
                    "parallelism": f"replicas x{world} (independent batches)"},
@@ -472,6 +483,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

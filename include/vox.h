@@ -267,6 +267,29 @@ vox_status vox_generate_noalloc(const vox_segment *d_segs, int64_t n, vox_dims d
                                 void *d_list, int64_t list_capacity, uint32_t *d_mask, int flags,
                                 int32_t *d_status, void *stream);
 
+/*
+ * Launch tuning (process-wide, every device). The outputs do not depend on it:
+ * only how the work is spread. Chosen by measurement (the Python autotuner).
+ *   run_len       voxels per thread run in the list/atomic generation kernel:
+ *                 16 or 32 (0 = default: 32; 64-bit lists always use 16)
+ *   volume_path   VOX_VOLUME_AUTO (bricks when the workspace allows) or
+ *                 VOX_VOLUME_ATOMIC (always per-voxel atomics)
+ *   ctas_per_sm   persistent CTAs per SM for the generation and brick kernels
+ *                 (0 = the occupancy maximum; larger values are capped there)
+ * vox_set_tuning(NULL) restores the defaults. Not to be changed while calls
+ * are being issued from other host threads.
+ */
+#define VOX_VOLUME_AUTO 0
+#define VOX_VOLUME_ATOMIC 1
+typedef struct vox_tuning {
+    int32_t run_len;
+    int32_t volume_path;
+    int32_t ctas_per_sm;
+    int32_t reserved;
+} vox_tuning;
+void vox_set_tuning(const vox_tuning *t);
+void vox_get_tuning(vox_tuning *t);
+
 /* Human-readable name of a status code. Never NULL. */
 const char *vox_strerror(int status);
 

@@ -29,6 +29,15 @@ constexpr int64_t kDefaultWaitNs = 500000000;  // 0.5 s bound on every in-kernel
 std::atomic<int64_t> g_stall_tile{-1};
 std::atomic<int64_t> g_wait_ns{kDefaultWaitNs};
 
+std::mutex g_tuning_mu;
+vox_tuning g_tuning{0, 0, 0, 0};
+
+vox_tuning current_tuning()
+{
+    std::lock_guard<std::mutex> lock(g_tuning_mu);
+    return g_tuning;
+}
+
 size_t align_up(size_t x) { return (x + kWsAlign - 1) & ~(kWsAlign - 1); }
 
 struct WsLayout {
@@ -287,19 +296,41 @@ vox_status launch_count_scan(const vox_segment *segs, int64_t n, vox_dims dims, 
     return cudaGetLastError() == cudaSuccess ? VOX_OK : VOX_ERR_CUDA;
 }
 
-template <int OUT, bool LIN64>
-vox_status launch_gen_t(const GenParams &p, cudaStream_t stream)
+// Persistent grid: SMs x CTAs per SM (occupancy maximum, or the tuned value
+// when it is smaller).
+int grid_ctas(const void *kernel, int threads, size_t smem)
 {
-    // run length: 32 voxels per thread, 16 when the 64-bit list doubles the staging
-    constexpr int R = (OUT & kOutList64) ? 16 : 32;
+    const int per_sm = blocks_per_sm(kernel, threads, smem);
+    const int sms = sm_count();
+    if (per_sm <= 0 || sms <= 0) return 0;
+    const vox_tuning tu = current_tuning();
+    const int use = (tu.ctas_per_sm > 0 && tu.ctas_per_sm < per_sm) ? tu.ctas_per_sm : per_sm;
+    return use * sms;
+}
+
+template <int R, int OUT, bool LIN64>
+vox_status launch_gen_r(const GenParams &p, cudaStream_t stream)
+{
     auto kernel = k_generate<R, OUT, LIN64>;
     const size_t smem = sizeof(GenSmem<R, OUT>);
     if (vox_status e = allow_smem(reinterpret_cast<const void *>(kernel), smem)) return e;
-    const int per_sm = blocks_per_sm(reinterpret_cast<const void *>(kernel), kGenThreads, smem);
-    const int sms = sm_count();
-    if (per_sm <= 0 || sms <= 0) return VOX_ERR_CUDA;
-    kernel<<<static_cast<unsigned>(per_sm * sms), kGenThreads, smem, stream>>>(p);
+    const int grid = grid_ctas(reinterpret_cast<const void *>(kernel), kGenThreads, smem);
+    if (grid <= 0) return VOX_ERR_CUDA;
+    kernel<<<static_cast<unsigned>(grid), kGenThreads, smem, stream>>>(p);
     return cudaGetLastError() == cudaSuccess ? VOX_OK : VOX_ERR_CUDA;
+}
+
+template <int OUT, bool LIN64>
+vox_status launch_gen_t(const GenParams &p, cudaStream_t stream)
+{
+    // run length: 32 voxels per thread by default, 16 when the 64-bit list
+    // doubles the staging; the tuning may ask for 16 with 32-bit outputs
+    if constexpr ((OUT & kOutList64) != 0) {
+        return launch_gen_r<16, OUT, LIN64>(p, stream);
+    } else {
+        if (current_tuning().run_len == 16) return launch_gen_r<16, OUT, LIN64>(p, stream);
+        return launch_gen_r<32, OUT, LIN64>(p, stream);
+    }
 }
 
 vox_status launch_generate(const vox_segment *segs, int64_t n, vox_dims dims, void *list, int64_t capacity,
@@ -404,9 +435,9 @@ vox_status launch_bricks(const vox_segment *segs, int64_t n, const BrickGeom &G,
     brp.use_tma = (mask != nullptr && make_volume_tmap(G, mask, &tmap)) ? 1 : 0;
     const size_t bsmem = sizeof(BrickSmem);
     if (vox_status e = allow_smem(reinterpret_cast<const void *>(k_brick_volume), bsmem)) return e;
-    const int per_sm = blocks_per_sm(reinterpret_cast<const void *>(k_brick_volume), kBrickThreads, bsmem);
-    if (per_sm <= 0) return VOX_ERR_CUDA;
-    k_brick_volume<<<static_cast<unsigned>(per_sm * sms), kBrickThreads, bsmem, stream>>>(brp, tmap);
+    const int bgrid = grid_ctas(reinterpret_cast<const void *>(k_brick_volume), kBrickThreads, bsmem);
+    if (bgrid <= 0) return VOX_ERR_CUDA;
+    k_brick_volume<<<static_cast<unsigned>(bgrid), kBrickThreads, bsmem, stream>>>(brp, tmap);
     if (cudaGetLastError() != cudaSuccess) return VOX_ERR_CUDA;
     return launch_generate(segs, n, dims, nullptr, 0, mask, VOX_OUT_BITMASK, ws, status, stream,
                            bp.brick_off + G.n_slots, capacity);
@@ -421,7 +452,7 @@ vox_status launch_outputs(const vox_segment *segs, int64_t n, vox_dims dims, voi
     if (n == 0) return VOX_OK;
     BrickGeom G;
     const bool bm = flags & VOX_OUT_BITMASK;
-    const bool bricks = bm && uses_bricks(n, dims, ws_bytes, &G);
+    const bool bricks = bm && current_tuning().volume_path != VOX_VOLUME_ATOMIC && uses_bricks(n, dims, ws_bytes, &G);
     if (!bricks) return launch_generate(segs, n, dims, list, capacity, mask, flags, ws, status, stream);
     const int list_flags = flags & (VOX_OUT_LIST32 | VOX_OUT_LIST64);
     if (list_flags) {
@@ -743,6 +774,25 @@ const char *vox_strerror(int status)
     case VOX_ERR_ALIGNMENT: return "buffer misaligned (segments and lists need 16 bytes)";
     default: return "unknown status";
     }
+}
+
+void vox_set_tuning(const vox_tuning *t)
+{
+    std::lock_guard<std::mutex> lock(g_tuning_mu);
+    if (t == nullptr) {
+        g_tuning = vox_tuning{0, 0, 0, 0};
+        return;
+    }
+    g_tuning = *t;
+    if (g_tuning.run_len != 16 && g_tuning.run_len != 32) g_tuning.run_len = 0;
+    if (g_tuning.volume_path < 0 || g_tuning.volume_path > VOX_VOLUME_ATOMIC) g_tuning.volume_path = 0;
+    if (g_tuning.ctas_per_sm < 0) g_tuning.ctas_per_sm = 0;
+    g_tuning.reserved = 0;
+}
+
+void vox_get_tuning(vox_tuning *t)
+{
+    if (t) *t = current_tuning();
 }
 
 void vox_debug_set_scan_stall(int64_t tile, int64_t wait_ns)

@@ -38,7 +38,16 @@ EXPORTED = (
     "vox_host_arena_size", "vox_generate_host", "vox_strerror", "vox_mask_words",
     "vox_debug_set_scan_stall", "vox_scan_tile_segments", "vox_generate_noalloc",
     "vox_workspace_size_volume", "vox_plan", "vox_workspace_size_batched", "vox_generate_batched",
+    "vox_set_tuning", "vox_get_tuning",
 )
+
+VOLUME_AUTO = 0
+VOLUME_ATOMIC = 1
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("run_len", ctypes.c_int32), ("volume_path", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 NOALLOC_MAX_SEGMENTS = 2000000
 
 
@@ -101,6 +110,10 @@ def load(path: str | None = None):
     lib.vox_workspace_size_batched.restype = sz
     lib.vox_generate_batched.argtypes = [vp, i64, vp, ctypes.c_int32, vp, i64, i32, vp, vp, sz, vp, vp]
     lib.vox_generate_batched.restype = i32
+    lib.vox_set_tuning.argtypes = [vp]
+    lib.vox_set_tuning.restype = None
+    lib.vox_get_tuning.argtypes = [vp]
+    lib.vox_get_tuning.restype = None
     lib.vox_generate_noalloc.argtypes = [vp, i64, Dims, vp, i64, vp, i32, vp, vp]
     lib.vox_generate_noalloc.restype = i32
     if path == _build.LIB:
@@ -158,6 +171,21 @@ def vox_plan(segs, dims, ws, status, stream=None):
 
 def vox_workspace_size_batched(n_total: int, n_scenes: int) -> int:
     return int(load().vox_workspace_size_batched(int(n_total), int(n_scenes)))
+
+
+def vox_set_tuning(run_len: int = 0, volume_path: int = 0, ctas_per_sm: int = 0) -> None:
+    t = Tuning(int(run_len), int(volume_path), int(ctas_per_sm), 0)
+    load().vox_set_tuning(ctypes.byref(t))
+
+
+def vox_reset_tuning() -> None:
+    load().vox_set_tuning(None)
+
+
+def vox_get_tuning() -> dict:
+    t = Tuning()
+    load().vox_get_tuning(ctypes.byref(t))
+    return {"run_len": t.run_len, "volume_path": t.volume_path, "ctas_per_sm": t.ctas_per_sm}
 
 
 def vox_mask_words(dims) -> int:
