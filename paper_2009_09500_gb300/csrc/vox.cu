@@ -175,7 +175,7 @@ bool make_geom(vox_dims dims, BrickGeom *G)
     }
     G->n_bricks = nb;
     G->reps = nb <= 32768 ? 8 : 1;
-    G->n_slots = nb * G->reps;
+    G->n_slots = nb * kPieceClasses * G->reps;
     return nb <= kMaxBricks && G->words <= kBrickWordsMax;
 }
 

@@ -44,13 +44,31 @@ struct BrickGeom {
     int32_t dim[3];     // volume extent
     int32_t words;      // words per brick, bxw * B[1] * B[2]
     int64_t n_bricks;
-    // Each brick has `reps` counters / cursors (segment s uses replica s % reps),
-    // brick-major, so that a brick's pieces stay contiguous after the scan while
-    // the atomics on one brick spread over `reps` addresses (few bricks, many
-    // pieces each: the counters would otherwise serialise).
+    // Pieces are bucketed by slot = (brick, length class, replica), brick-major,
+    // classes longest first: after the scan a brick's pieces are contiguous and
+    // already ordered by length, so that a warp taking 32 consecutive pieces gets
+    // pieces of similar length. Each (brick, class) has `reps` counters (segment
+    // s uses replica s % reps) so that atomics on one brick spread over several
+    // addresses when there are few bricks with many pieces each.
     int32_t reps;
-    int64_t n_slots;    // n_bricks * reps
+    int64_t n_slots;    // n_bricks * kPieceClasses * reps
 };
+
+constexpr int kPieceClasses = 22;  // half octaves of the piece length (<= 1024)
+
+// Length class of a piece, longest first: 0 for the longest half octave.
+__device__ __forceinline__ int32_t piece_class_desc(int32_t len)
+{
+    const uint32_t l = static_cast<uint32_t>(len);
+    const int32_t oct = 31 - __clz(l);
+    const int32_t cls = 2 * oct + (oct > 0 ? static_cast<int32_t>((l >> (oct - 1)) & 1u) : 0);
+    return kPieceClasses - 1 - cls;
+}
+
+__device__ __forceinline__ int64_t piece_slot(const BrickGeom &G, int64_t brick, int32_t len, int32_t rep)
+{
+    return (brick * kPieceClasses + piece_class_desc(len)) * G.reps + rep;
+}
 
 __device__ __forceinline__ int64_t brick_index(const BrickGeom &G, int32_t b0, int32_t b1, int32_t b2)
 {
@@ -160,7 +178,7 @@ __global__ void __launch_bounds__(256) k_bin_count(BinParams p)
     load_record(p.segs, s, r);
     if (!endpoints_inside(r, p.G)) return;  // reported by the count kernel
     const int32_t rep = static_cast<int32_t>(s % p.G.reps);
-    for_each_piece(r, p.G, [&](int64_t b, int32_t, int32_t) { atomicAdd(p.brick_count + b * p.G.reps + rep, 1); });
+    for_each_piece(r, p.G, [&](int64_t b, int32_t, int32_t len) { atomicAdd(p.brick_count + piece_slot(p.G, b, len, rep), 1); });
 }
 
 // One segment per thread.
@@ -193,7 +211,7 @@ __global__ void __launch_bounds__(256) k_bin_scatter(BinParams p)
 #pragma unroll
         for (int e = 0; e < kBatch; ++e)
             if (e == nb) {
-                bb[e] = b * p.G.reps + rep;
+                bb[e] = piece_slot(p.G, b, len, rep);
                 val[e] = pack_piece(s, k, len);
             }
         if (++nb == kBatch) flush();
@@ -267,43 +285,38 @@ __device__ __forceinline__ void merge_brick(const uint32_t *bits, const BrickGeo
     }
 }
 
-constexpr int kChunk = 512;        // pieces staged per round (with their segment records)
-constexpr int kLenClasses = 11;    // piece length classes: floor(log2(len)), len <= 1024
-
 struct BrickSmem {
     alignas(128) uint32_t bits[kBrickWordsMax];  // also the TMA source tile (128-byte aligned)
-    alignas(16) int32_t rec[kChunk * 6];
-    uint64_t pc[kChunk];
-    uint16_t order[kChunk];
-    int32_t cls[2 * kLenClasses];  // counts, then cursors
     int32_t origin[3];
-    int32_t next_group;            // next group of 32 ordered pieces to hand to a warp
+    int32_t next_group;  // next group of 32 pieces of the brick to hand to a warp
     int64_t brick;
 };
 
-// One CTA per brick (dynamic tickets). Pieces are staged kChunk at a time with
-// their segment records; inside a chunk they are ordered by length class
-// (floor(log2(len))), longest first, and warps take groups of 32 consecutive
-// pieces from a shared counter: the 32 lanes of a warp walk pieces of similar
-// length, and the warps share the chunk's work as it comes (longest groups
-// first, so the tail is short). Each lane enters its piece's segment at the
-// piece's first step (one division per minor axis) and steps through it with
-// the carry recurrence, OR-ing bits into the brick's shared bitmap.
+// One CTA per brick (dynamic tickets). The brick's pieces arrive ordered by
+// length class, longest first (the bucket order of the binning), and warps take
+// groups of 32 consecutive pieces from a shared counter: the lanes of a warp
+// walk pieces of similar length and the warps share the brick's work as it
+// comes, longest groups first. Each lane loads its piece and its segment's
+// record, enters the segment at the piece's first step (one division per minor
+// axis) and steps through the piece with the carry recurrence, OR-ing bits into
+// the brick's shared bitmap; the bitmap is then merged into the volume.
 __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, const __grid_constant__ CUtensorMap tmap)
 {
-    static_assert(kChunk == 2 * kBrickThreads, "two pieces per thread per chunk");
     extern __shared__ __align__(128) unsigned char brick_smem_raw[];
     BrickSmem &sm = *reinterpret_cast<BrickSmem *>(brick_smem_raw);
     const int t = threadIdx.x;
+    const int lane = t & 31;
     if (ld_volatile_i32(p.status) != 0) return;
     if (__ldg(p.brick_off + p.G.n_slots) > p.capacity) return;  // pieces did not fit: atomics path
     const BrickGeom &G = p.G;
+    const int64_t slots_per_brick = static_cast<int64_t>(kPieceClasses) * G.reps;
     const uint32_t bw = static_cast<uint32_t>(G.B[0]);
     const uint32_t bwh = static_cast<uint32_t>(G.B[0]) * static_cast<uint32_t>(G.B[1]);
     while (true) {
         if (t == 0) {
             const int64_t b = atomicAdd(p.ticket, 1u);
             sm.brick = b;
+            sm.next_group = 0;
             if (b < G.n_bricks) {
                 const int64_t rest = b / G.nb[0];
                 sm.origin[0] = static_cast<int32_t>(b - rest * G.nb[0]) * G.B[0];
@@ -314,77 +327,55 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
         __syncthreads();
         const int64_t b = sm.brick;
         const int32_t X0 = sm.origin[0], Y0 = sm.origin[1], Z0 = sm.origin[2];
-        __syncthreads();  // the ticket slot is rewritten only after everyone has read it
         if (b >= G.n_bricks) break;
-        const int64_t lo = __ldg(p.brick_off + b * G.reps), hi = __ldg(p.brick_off + (b + 1) * G.reps);
-        if (lo == hi) continue;
+        const int64_t lo = __ldg(p.brick_off + b * slots_per_brick);
+        const int64_t hi = __ldg(p.brick_off + (b + 1) * slots_per_brick);
+        if (lo == hi) {
+            __syncthreads();  // everyone has read the ticket slot before it is rewritten
+            continue;
+        }
         if (p.use_tma) {  // the previous brick's reduction must have read the tile
             if (t == 0) bulk_wait_read_all();
-            __syncthreads();
         }
+        __syncthreads();
         for (int q = t; q < G.words; q += kBrickThreads) sm.bits[q] = 0u;
+        __syncthreads();
         // brick-local bit index of (x, y, z): (x - X0) + B0 (y - Y0) + B0 B1 (z - Z0),
         // kept modulo 2^32 while stepping (only the local value is ever used)
         const uint32_t origin = static_cast<uint32_t>(X0) + static_cast<uint32_t>(Y0) * bw +
                                 static_cast<uint32_t>(Z0) * bwh;
-        for (int64_t c0 = lo; c0 < hi; c0 += kChunk) {
-            const int32_t cnt = static_cast<int32_t>(min(static_cast<int64_t>(kChunk), hi - c0));
-            if (t < 2 * kLenClasses) sm.cls[t] = 0;
-            __syncthreads();  // previous chunk done, class counters cleared
-            // ---- stage the chunk and count pieces per length class
-            int32_t cls2[2];
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const int i = t + e * kBrickThreads;
-                cls2[e] = -1;
-                if (i < cnt) {
-                    const uint64_t pc = __ldg(p.pieces + c0 + i);
-                    sm.pc[i] = pc;
-                    const uint32_t len = static_cast<uint32_t>(pc >> 54) + 1u;
-                    cls2[e] = 31 - __clz(len);
-                    atomicAdd(sm.cls + cls2[e], 1);
-                    load_record(p.segs, static_cast<int64_t>(pc & 0xffffffffull), sm.rec + 6 * i);
-                }
-            }
-            __syncthreads();
-            if (t == 0) {
-                int32_t run = 0;
-                for (int c = kLenClasses - 1; c >= 0; --c) {  // longest class first
-                    sm.cls[kLenClasses + c] = run;
-                    run += sm.cls[c];
-                }
-                sm.next_group = 0;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int e = 0; e < 2; ++e)
-                if (cls2[e] >= 0) sm.order[atomicAdd(sm.cls + kLenClasses + cls2[e], 1)] = static_cast<uint16_t>(t + e * kBrickThreads);
-            __syncthreads();
-            // ---- one piece per lane; warps take groups of 32 ordered pieces
-            const int lane = t & 31;
+        const int64_t cnt = hi - lo;
 #pragma unroll 1
-            while (true) {
-                int32_t grp = 0;
-                if (lane == 0) grp = atomicAdd(&sm.next_group, 1);
-                grp = __shfl_sync(0xffffffffu, grp, 0);
-                if (grp * 32 >= cnt) break;
-                const int j = grp * 32 + lane;
-                if (j < cnt) {
-                    const int i = sm.order[j];
-                    const uint64_t pc = sm.pc[i];
-                    const int32_t len = static_cast<int32_t>(pc >> 54) + 1;
-                    Stepper<uint32_t, uint32_t> st;
-                    st.enter(sm.rec + 6 * i, static_cast<int32_t>((pc >> 32) & 0x3fffffull), bw, bwh);
-                    st.L -= origin;
-                    // one shared-memory atomic per voxel: cheaper than branching to
-                    // merge runs of the same word (measured on both workload shapes)
-                    for (int32_t e = 0; e < len; ++e) {
+        while (true) {
+            int32_t grp = 0;
+            if (lane == 0) grp = atomicAdd(&sm.next_group, 1);
+            grp = __shfl_sync(0xffffffffu, grp, 0);
+            if (static_cast<int64_t>(grp) * 32 >= cnt) break;
+            const int64_t j = static_cast<int64_t>(grp) * 32 + lane;
+            if (j < cnt) {
+                const uint64_t pc = __ldg(p.pieces + lo + j);
+                const int32_t len = static_cast<int32_t>(pc >> 54) + 1;
+                int32_t rec[6];
+                load_record(p.segs, static_cast<int64_t>(pc & 0xffffffffull), rec);
+                Stepper<uint32_t, uint32_t> st;
+                st.enter(rec, static_cast<int32_t>((pc >> 32) & 0x3fffffull), bw, bwh);
+                st.L -= origin;
+                // one shared-memory atomic per voxel: cheaper than branching to
+                // merge runs of the same word (measured on both workload shapes)
+                int32_t e = 0;
+                for (; e + 4 <= len; e += 4) {
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
                         atomicOr(sm.bits + (st.L >> 5), 1u << (st.L & 31u));
                         st.template step<false, true>();
                     }
                 }
-                __syncwarp();
+                for (; e < len; ++e) {
+                    atomicOr(sm.bits + (st.L >> 5), 1u << (st.L & 31u));
+                    st.template step<false, true>();
+                }
             }
+            __syncwarp();
         }
         __syncthreads();
         if (p.use_tma) {

@@ -443,8 +443,21 @@ __global__ void __launch_bounds__(kGenThreads, 3) k_generate(GenParams p)
                 int32_t u = 0;
                 while (true) {
                     const int32_t m = min(st.left + 1, len - u);  // voxels taken from this segment
-#pragma unroll 2
-                    for (int32_t e = 0; e < m; ++e) {
+                    int32_t e = 0;
+                    if constexpr (kList && !kMask) {
+                        // four voxels per iteration: stores at fixed offsets from one pointer
+                        for (; e + 4 <= m; e += 4) {
+#pragma unroll
+                            for (int v = 0; v < 4; ++v) {
+                                sp[v * S] = static_cast<uint32_t>(st.P);
+                                if (L::kWide)
+                                    sp[R * S + v * S] = static_cast<uint32_t>(static_cast<uint64_t>(st.P) >> 32);
+                                st.template step<true, false>();
+                            }
+                            sp += 4 * S;
+                        }
+                    }
+                    for (; e < m; ++e) {
                         if (kList) {
                             sp[0] = static_cast<uint32_t>(st.P);
                             if (L::kWide) sp[R * S] = static_cast<uint32_t>(static_cast<uint64_t>(st.P) >> 32);
@@ -481,13 +494,14 @@ __global__ void __launch_bounds__(kGenThreads, 3) k_generate(GenParams p)
                 const int32_t n4 = pass_len >> 2;
                 for (int32_t q = t; q < n4; q += kGenThreads) {
                     const int32_t p0 = 4 * q;
+                    // voxels p0 .. p0+3 sit in slots p0 % R .. +3 of thread p0 / R
+                    // (R is a multiple of 4): one base index, three fixed strides
+                    const uint32_t *src = sm.stage + (p0 % R) * S + p0 / R;
                     uint32_t lo[4], hi[4];
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        const int32_t pe = p0 + e;
-                        const int32_t idx = (pe % R) * S + pe / R;
-                        lo[e] = sm.stage[idx];
-                        if (L::kWide) hi[e] = sm.stage[R * S + idx];
+                        lo[e] = src[e * S];
+                        if (L::kWide) hi[e] = src[R * S + e * S];
                     }
                     if constexpr (L::kWide) {
                         ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(list + gp + p0);
