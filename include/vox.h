@@ -18,7 +18,13 @@
  *   VOX_OUT_BITMASK  occupancy volume, one bit per voxel: voxel (x, y, z) is bit
  *                    b = x + w*(y + h*z), i.e. bit (b % 32) of uint32 word b / 32;
  *                    ceil(w*h*d / 32) words. Bits are OR-ed in: the caller clears
- *                    the volume when it wants a fresh one.
+ *                    the volume when it wants a fresh one, or adds VOX_OUT_FRESH.
+ *   VOX_OUT_FRESH    (with VOX_OUT_BITMASK only) the call writes the whole volume:
+ *                    afterwards it holds exactly these segments' voxels, whatever
+ *                    it held before. The brick path stores each brick whole
+ *                    (no read of the old volume); the other paths clear the volume
+ *                    first. If the call fails on the device (*d_status != 0), the
+ *                    volume is either unchanged or cleared.
  *   The list holds the voxels of segment 0 (k = 0..N), then segment 1, and so on:
  *   voxel k of segment s sits at index offsets[s] + k, offsets being the exclusive
  *   prefix sum of the per-segment counts N + 1. Voxels shared by two segments
@@ -76,6 +82,7 @@ typedef struct vox_dims {
 #define VOX_OUT_LIST32 1
 #define VOX_OUT_LIST64 2
 #define VOX_OUT_BITMASK 4
+#define VOX_OUT_FRESH 8
 
 /* Bytes of workspace a call on n segments needs (count, scan and generation of
  * one scene). The workspace is device memory, 256-byte aligned, caller-owned,
@@ -110,10 +117,11 @@ vox_status vox_count(const vox_segment *d_segs, int64_t n, vox_dims dims,
  *                    aligned) or NULL when no list flag is set
  *   list_capacity    elements available in d_list; V above it is
  *                    VOX_ERR_CAPACITY (device) and nothing is written
- *   d_mask           device uint32[ceil(w*h*d/32)], 4-byte aligned, OR-ed into;
- *                    NULL when VOX_OUT_BITMASK is not set
+ *   d_mask           device uint32[ceil(w*h*d/32)], 4-byte aligned, OR-ed into
+ *                    (overwritten with VOX_OUT_FRESH); NULL when
+ *                    VOX_OUT_BITMASK is not set
  *   flags            VOX_OUT_LIST32 or VOX_OUT_LIST64 (not both), optionally
- *                    | VOX_OUT_BITMASK; at least one output
+ *                    | VOX_OUT_BITMASK (| VOX_OUT_FRESH); at least one output
  *   d_ws, ws_bytes   workspace of at least vox_workspace_size(n) bytes
  *   d_status         as for vox_count
  */
@@ -199,7 +207,8 @@ size_t vox_workspace_size_batched(int64_t n_total, int32_t n_scenes);
  *                   order, k = 0..N per segment; list_capacity elements; every
  *                   scene must have edges <= 1024 for LIST32
  *   flags           list format and/or VOX_OUT_BITMASK (each scene's voxels are
- *                   OR-ed into that scene's mask; scenes with mask NULL skip it)
+ *                   OR-ed into that scene's mask; scenes with mask NULL skip it);
+ *                   VOX_OUT_FRESH clears every scene's mask first
  *   d_scene_base    device int64[n_scenes + 1] receiving base[k] (first voxel of
  *                   scene k in the list) and base[n_scenes] = total V, or NULL
  *   d_ws, ws_bytes  at least vox_workspace_size_batched(n_total, n_scenes)
@@ -221,7 +230,8 @@ vox_status vox_generate_batched(const vox_segment *d_segs, int64_t n_total, cons
  *   h_segs          host vox_segment[n] (pinned memory for full copy speed)
  *   h_list          host list of list_capacity elements, or NULL
  *   h_mask          host uint32[ceil(w*h*d/32)], OVERWRITTEN with the volume of
- *                   these segments alone (not OR-ed), or NULL
+ *                   these segments alone (not OR-ed; VOX_OUT_FRESH changes
+ *                   nothing here), or NULL
  *   d_arena         device scratch of vox_host_arena_size(...) bytes, 256-byte aligned
  *   h_total         receives V (may be NULL)
  *   returns         VOX_OK or the first error, host or device

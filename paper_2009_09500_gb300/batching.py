@@ -95,8 +95,9 @@ def make_batch(workloads_list, flags=vox.OUT_LIST32 | vox.OUT_BITMASK, device="c
     d = np.abs(segs_np[:, 3:].astype(np.int64) - segs_np[:, :3])
     V = int((d.max(axis=1) + 1).sum()) if len(segs_np) else 0
     masks = []
-    if flags & vox.OUT_BITMASK:
-        masks = [torch.zeros(vox.vox_mask_words(dm), dtype=torch.int32, device=device) for dm in dims]
+    if flags & vox.OUT_BITMASK:  # fresh volumes are cleared by the launch itself
+        alloc = torch.empty if flags & vox.OUT_FRESH else torch.zeros
+        masks = [alloc(vox.vox_mask_words(dm), dtype=torch.int32, device=device) for dm in dims]
     ptrs = [m.data_ptr() for m in masks] if masks else [0] * len(dims)
     table = scene_table_bytes(seg_counts, dims, ptrs)
     scenes = torch.frombuffer(bytearray(table), dtype=torch.uint8).to(device)

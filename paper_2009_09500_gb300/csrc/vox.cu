@@ -128,9 +128,10 @@ vox_status check_generate_args(const vox_segment *segs, int64_t n, vox_dims dims
     if (n < 0 || status == nullptr) return VOX_ERR_INVALID_ARG;
     if (n > 0 && segs == nullptr) return VOX_ERR_INVALID_ARG;
     if (vox_status e = check_dims(dims)) return e;
-    if (flags & ~(VOX_OUT_LIST32 | VOX_OUT_LIST64 | VOX_OUT_BITMASK)) return VOX_ERR_INVALID_ARG;
+    if (flags & ~(VOX_OUT_LIST32 | VOX_OUT_LIST64 | VOX_OUT_BITMASK | VOX_OUT_FRESH)) return VOX_ERR_INVALID_ARG;
     const bool l32 = flags & VOX_OUT_LIST32, l64 = flags & VOX_OUT_LIST64, bm = flags & VOX_OUT_BITMASK;
     if (!(l32 || l64 || bm) || (l32 && l64)) return VOX_ERR_INVALID_ARG;
+    if ((flags & VOX_OUT_FRESH) && !bm) return VOX_ERR_INVALID_ARG;
     if (l32 && (dims.w > 1024 || dims.h > 1024 || dims.d > 1024)) return VOX_ERR_PACK_WIDTH;
     if ((l32 || l64) && (list == nullptr || capacity < 0)) return VOX_ERR_INVALID_ARG;
     if (bm && mask == nullptr) return VOX_ERR_INVALID_ARG;
@@ -168,6 +169,10 @@ bool make_geom(vox_dims dims, BrickGeom *G)
     G->dim[2] = dims.d;
     G->row_words = dims.w / 32;
     G->words = G->bxw * G->B[1] * G->B[2];
+    for (int a = 0; a < 3; ++a) {
+        G->logB[a] = 0;
+        while ((1 << G->logB[a]) < G->B[a]) ++G->logB[a];
+    }
     int64_t nb = 1;
     for (int a = 0; a < 3; ++a) {
         G->nb[a] = (G->dim[a] + G->B[a] - 1) / G->B[a];
@@ -377,7 +382,8 @@ vox_status launch_generate(const vox_segment *segs, int64_t n, vox_dims dims, vo
 // bin -> scan -> scatter -> per-brick volume, then the atomic kernel, which only
 // runs if the pieces did not fit in the workspace
 vox_status launch_bricks(const vox_segment *segs, int64_t n, const BrickGeom &G, vox_dims dims, uint32_t *mask,
-                         void *ws, size_t ws_bytes, int32_t *status, cudaStream_t stream, bool count_only = false)
+                         void *ws, size_t ws_bytes, int32_t *status, cudaStream_t stream, bool count_only = false,
+                         bool fresh = false)
 {
     // the brick counts come from the count + scan (k_bin_count); the
     // tickets and look-back flags of this pass are reset here, so that the pass
@@ -433,6 +439,7 @@ vox_status launch_bricks(const vox_segment *segs, int64_t n, const BrickGeom &G,
     CUtensorMap tmap;
     std::memset(&tmap, 0, sizeof(tmap));
     brp.use_tma = (mask != nullptr && make_volume_tmap(G, mask, &tmap)) ? 1 : 0;
+    brp.fresh = fresh ? 1 : 0;
     const size_t bsmem = sizeof(BrickSmem);
     if (vox_status e = allow_smem(reinterpret_cast<const void *>(k_brick_volume), bsmem)) return e;
     const int bgrid = grid_ctas(reinterpret_cast<const void *>(k_brick_volume), kBrickThreads, bsmem);
@@ -449,17 +456,24 @@ vox_status launch_bricks(const vox_segment *segs, int64_t n, const BrickGeom &G,
 vox_status launch_outputs(const vox_segment *segs, int64_t n, vox_dims dims, void *list, int64_t capacity,
                           uint32_t *mask, int flags, void *ws, size_t ws_bytes, int32_t *status, cudaStream_t stream)
 {
-    if (n == 0) return VOX_OK;
     BrickGeom G;
     const bool bm = flags & VOX_OUT_BITMASK;
-    const bool bricks = bm && current_tuning().volume_path != VOX_VOLUME_ATOMIC && uses_bricks(n, dims, ws_bytes, &G);
-    if (!bricks) return launch_generate(segs, n, dims, list, capacity, mask, flags, ws, status, stream);
+    const bool fresh = bm && (flags & VOX_OUT_FRESH);
+    const bool bricks =
+        n > 0 && bm && current_tuning().volume_path != VOX_VOLUME_ATOMIC && uses_bricks(n, dims, ws_bytes, &G);
+    if (!bricks) {
+        // a fresh volume without the brick path: cleared first, then OR-ed into
+        if (fresh && cudaMemsetAsync(mask, 0, 4 * static_cast<size_t>(vox_mask_words(dims)), stream) != cudaSuccess)
+            return VOX_ERR_CUDA;
+        if (n == 0) return VOX_OK;
+        return launch_generate(segs, n, dims, list, capacity, mask, flags, ws, status, stream);
+    }
     const int list_flags = flags & (VOX_OUT_LIST32 | VOX_OUT_LIST64);
     if (list_flags) {
         if (vox_status e = launch_generate(segs, n, dims, list, capacity, nullptr, list_flags, ws, status, stream))
             return e;
     }
-    return launch_bricks(segs, n, G, dims, mask, ws, ws_bytes, status, stream);
+    return launch_bricks(segs, n, G, dims, mask, ws, ws_bytes, status, stream, false, fresh);
 }
 
 // ---- batched scenes ----------------------------------------------------------
@@ -573,8 +587,10 @@ vox_status vox_generate(const vox_segment *d_segs, int64_t n, vox_dims dims, voi
         return e;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), s) != cudaSuccess) return VOX_ERR_CUDA;
-    if (n == 0) return VOX_OK;
-    if (vox_status e = launch_count_scan(d_segs, n, dims, nullptr, nullptr, d_ws, ws_bytes, d_status, s)) return e;
+    if (n > 0) {
+        if (vox_status e = launch_count_scan(d_segs, n, dims, nullptr, nullptr, d_ws, ws_bytes, d_status, s))
+            return e;
+    }
     return launch_outputs(d_segs, n, dims, d_list, list_capacity, d_mask, flags, d_ws, ws_bytes, d_status, s);
 }
 
@@ -601,9 +617,10 @@ vox_status vox_generate_batched(const vox_segment *d_segs, int64_t n_total, cons
 {
     if (n_total < 0 || n_scenes < 1 || d_scenes == nullptr || d_status == nullptr) return VOX_ERR_INVALID_ARG;
     if (n_total > 0 && d_segs == nullptr) return VOX_ERR_INVALID_ARG;
-    if (flags & ~(VOX_OUT_LIST32 | VOX_OUT_LIST64 | VOX_OUT_BITMASK)) return VOX_ERR_INVALID_ARG;
+    if (flags & ~(VOX_OUT_LIST32 | VOX_OUT_LIST64 | VOX_OUT_BITMASK | VOX_OUT_FRESH)) return VOX_ERR_INVALID_ARG;
     const bool l32 = flags & VOX_OUT_LIST32, l64 = flags & VOX_OUT_LIST64, bm = flags & VOX_OUT_BITMASK;
     if (!(l32 || l64 || bm) || (l32 && l64)) return VOX_ERR_INVALID_ARG;
+    if ((flags & VOX_OUT_FRESH) && !bm) return VOX_ERR_INVALID_ARG;
     if ((l32 || l64) && (d_list == nullptr || list_capacity < 0)) return VOX_ERR_INVALID_ARG;
     if (n_total > 0 && !aligned(d_segs, 16)) return VOX_ERR_ALIGNMENT;
     if ((l32 || l64) && !aligned(d_list, 16)) return VOX_ERR_ALIGNMENT;
@@ -618,6 +635,10 @@ vox_status vox_generate_batched(const vox_segment *d_segs, int64_t n_total, cons
     k_scene_map<<<static_cast<unsigned>(n_scenes), 256, 0, s>>>(scenes, n_scenes, n_total, scene_of, d_status,
                                                                  l32 ? 1 : 0);
     if (cudaGetLastError() != cudaSuccess) return VOX_ERR_CUDA;
+    if (bm && (flags & VOX_OUT_FRESH)) {  // every scene's volume cleared (a valid table only)
+        k_scene_clear<<<dim3(kSceneClearCtas, static_cast<unsigned>(n_scenes)), 256, 0, s>>>(scenes, d_status);
+        if (cudaGetLastError() != cudaSuccess) return VOX_ERR_CUDA;
+    }
     if (n_total > 0) {
         const vox_dims unused{1, 1, 1};
         if (vox_status e = launch_count_scan(d_segs, n_total, unused, nullptr, nullptr, d_ws, ws_bytes, d_status, s,

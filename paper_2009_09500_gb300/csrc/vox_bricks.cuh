@@ -30,12 +30,13 @@
 
 namespace vox {
 
-constexpr int kBrickThreads = 256;
-constexpr int kBrickWordsMax = 8192;  // 32 KB shared bitmap per brick
+constexpr int kBrickThreads = 512;
+constexpr int kBrickWordsMax = 16384;  // 64 KB shared bitmap per brick
 constexpr int32_t kNoStep = 0x7fffffff;
 
 struct BrickGeom {
     int32_t B[3];       // brick extent in voxels per axis (powers of two, B[0] >= 32)
+    int32_t logB[3];    // log2(B[a])
     int32_t nb[3];      // bricks per axis
     int32_t bxw;        // words per brick row, B[0] / 32
     int32_t log_bxw;    // log2(bxw)
@@ -50,7 +51,7 @@ struct BrickGeom {
     // pieces of similar length. Each (brick, class) has `reps` counters (segment
     // s uses replica s % reps) so that atomics on one brick spread over several
     // addresses when there are few bricks with many pieces each.
-    int32_t reps;
+    int32_t reps;       // 1 or 8 (segment s uses replica s & (reps - 1))
     int64_t n_slots;    // n_bricks * kPieceClasses * reps
 };
 
@@ -65,71 +66,103 @@ __device__ __forceinline__ int32_t piece_class_desc(int32_t len)
     return kPieceClasses - 1 - cls;
 }
 
-__device__ __forceinline__ int64_t piece_slot(const BrickGeom &G, int64_t brick, int32_t len, int32_t rep)
+// Slots fit 31 bits: with 8 replicas there are at most 32768 bricks, else at
+// most 2^26 bricks and one replica.
+__device__ __forceinline__ uint32_t piece_slot(const BrickGeom &G, int32_t brick, int32_t len, int32_t rep)
 {
-    return (brick * kPieceClasses + piece_class_desc(len)) * G.reps + rep;
+    return (static_cast<uint32_t>(brick) * kPieceClasses + static_cast<uint32_t>(piece_class_desc(len))) *
+               static_cast<uint32_t>(G.reps) +
+           static_cast<uint32_t>(rep);
 }
 
-__device__ __forceinline__ int64_t brick_index(const BrickGeom &G, int32_t b0, int32_t b1, int32_t b2)
-{
-    return b0 + static_cast<int64_t>(G.nb[0]) * (b1 + static_cast<int64_t>(G.nb[1]) * b2);
-}
+// Crossing steps of one axis. The segment's offset on the axis,
+// q(k) = floor((2 k A + N) / (2 N)), first reaches Q at
+// k = ceil(N (2Q - 1) / (2A)) (for 1 <= Q <= A <= N). Along the segment the
+// axis enters a new brick at Q_1, Q_1 + B, Q_1 + 2B, ...: with
+// T_j = N (2 Q_j - 1) + 2A - 1 = 2A k_j + rem_j, one division gives k_1 and
+// rem_1, and each later crossing follows from T_{j+1} = T_j + 2NB without a
+// division, 2NB = 2A qs + rs having been divided once.
+struct AxisCrossings {
+    int32_t left;  // crossings still ahead
+    int32_t nk;    // step of the next crossing (kNoStep when none)
+    int32_t rem;   // T_j mod 2A for the crossing at nk
+    int32_t qs, rs;
+    int32_t twoA;
 
-// Smallest step k with floor((2 k A + N) / (2 N)) >= Q, for 1 <= Q <= A <= N:
-// k = ceil(N (2Q - 1) / (2A)).
-__device__ __forceinline__ int32_t first_step_reaching(int32_t A, int32_t N, int32_t Q)
-{
-    if (N <= 46340) {  // N (2Q - 1) + 2A - 1 < 2 N^2 + 2N < 2^32
-        const uint32_t num = static_cast<uint32_t>(N) * static_cast<uint32_t>(2 * Q - 1);
-        const uint32_t den = 2u * static_cast<uint32_t>(A);
-        return static_cast<int32_t>((num + den - 1u) / den);
+    __device__ __forceinline__ void init(int32_t S, int32_t E, int32_t A, int32_t N, int32_t logB)
+    {
+        const int32_t b0 = S >> logB, be = E >> logB;  // coordinates are inside the volume (>= 0)
+        left = abs(be - b0);
+        nk = kNoStep;
+        if (left == 0) return;
+        const int32_t B = 1 << logB;
+        const int32_t Q = be > b0 ? (b0 + 1) * B - S : S - b0 * B + 1;
+        twoA = 2 * A;
+        if (N <= 46340) {  // T < 2 N^2 + 2N < 2^32
+            const uint32_t T = static_cast<uint32_t>(N) * static_cast<uint32_t>(2 * Q - 1) + static_cast<uint32_t>(twoA - 1);
+            const uint32_t k = T / static_cast<uint32_t>(twoA);
+            nk = static_cast<int32_t>(k);
+            rem = static_cast<int32_t>(T - k * static_cast<uint32_t>(twoA));
+        } else {
+            const uint64_t T = static_cast<uint64_t>(N) * static_cast<uint64_t>(2 * Q - 1) + static_cast<uint64_t>(twoA - 1);
+            const uint64_t k = T / static_cast<uint64_t>(twoA);
+            nk = static_cast<int32_t>(k);
+            rem = static_cast<int32_t>(T - k * static_cast<uint64_t>(twoA));
+        }
+        if (left > 1) {  // 2NB < 2^31 (N < 2^21, B <= 256)
+            const uint32_t step = 2u * static_cast<uint32_t>(N) * static_cast<uint32_t>(B);
+            const uint32_t q = step / static_cast<uint32_t>(twoA);
+            qs = static_cast<int32_t>(q);
+            rs = static_cast<int32_t>(step - q * static_cast<uint32_t>(twoA));
+        }
     }
-    const uint64_t num = static_cast<uint64_t>(N) * static_cast<uint64_t>(2 * Q - 1);
-    const uint64_t den = 2ull * static_cast<uint64_t>(A);
-    return static_cast<int32_t>((num + den - 1ull) / den);
-}
+
+    __device__ __forceinline__ void advance()
+    {
+        if (--left == 0) {
+            nk = kNoStep;
+            return;
+        }
+        nk += qs;
+        rem += rs;
+        if (rem >= twoA) {
+            rem -= twoA;
+            ++nk;
+        }
+    }
+};
 
 // Calls f(brick, k_lo, len) for every maximal run of consecutive steps of the
 // segment that stays in one brick, in increasing k. Endpoints must be inside
-// the volume.
+// the volume. Brick indices fit 32 bits (at most 2^26 bricks).
 template <typename F>
 __device__ __forceinline__ void for_each_piece(const int32_t *rec, const BrickGeom &G, F &&f)
 {
-    int32_t S[3], A[3], b0[3], b[3], dir[3], left[3], j[3], nk[3];
+    AxisCrossings ax[3];
+    int32_t A[3], bstep[3];
     int32_t N = 0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        S[a] = rec[a];
-        const int32_t d = rec[3 + a] - rec[a];
-        A[a] = abs(d);
+        A[a] = abs(rec[3 + a] - rec[a]);
         N = max(N, A[a]);
-        b0[a] = S[a] / G.B[a];
-        const int32_t be = rec[3 + a] / G.B[a];
-        b[a] = b0[a];
-        dir[a] = be > b0[a] ? 1 : (be < b0[a] ? -1 : 0);
-        left[a] = abs(be - b0[a]);
-        j[a] = 1;
     }
-    // step at which axis a enters its next brick (the j-th crossing)
-    auto next_cross = [&](int a) -> int32_t {
-        if (left[a] == 0) return kNoStep;
-        const int32_t Q = dir[a] > 0 ? (b0[a] + j[a]) * G.B[a] - S[a] : S[a] - ((b0[a] - j[a] + 1) * G.B[a] - 1);
-        return first_step_reaching(A[a], N, Q);
-    };
+    int32_t brick = (rec[0] >> G.logB[0]) + G.nb[0] * ((rec[1] >> G.logB[1]) + G.nb[1] * (rec[2] >> G.logB[2]));
+    const int32_t stride[3] = {1, G.nb[0], G.nb[0] * G.nb[1]};
 #pragma unroll
-    for (int a = 0; a < 3; ++a) nk[a] = next_cross(a);
+    for (int a = 0; a < 3; ++a) {
+        ax[a].init(rec[a], rec[3 + a], A[a], N, G.logB[a]);
+        bstep[a] = rec[3 + a] >= rec[a] ? stride[a] : -stride[a];
+    }
     int32_t k = 0;
     while (true) {
-        const int32_t kn = min(min(nk[0], nk[1]), min(nk[2], N + 1));
-        f(brick_index(G, b[0], b[1], b[2]), k, kn - k);
+        const int32_t kn = min(min(ax[0].nk, ax[1].nk), min(ax[2].nk, N + 1));
+        f(brick, k, kn - k);
         if (kn > N) break;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            if (nk[a] == kn) {
-                b[a] += dir[a];
-                --left[a];
-                ++j[a];
-                nk[a] = next_cross(a);
+            if (ax[a].nk == kn) {
+                brick += bstep[a];
+                ax[a].advance();
             }
         }
         k = kn;
@@ -177,8 +210,8 @@ __global__ void __launch_bounds__(256) k_bin_count(BinParams p)
     int32_t r[6];
     load_record(p.segs, s, r);
     if (!endpoints_inside(r, p.G)) return;  // reported by the count kernel
-    const int32_t rep = static_cast<int32_t>(s % p.G.reps);
-    for_each_piece(r, p.G, [&](int64_t b, int32_t, int32_t len) { atomicAdd(p.brick_count + piece_slot(p.G, b, len, rep), 1); });
+    const int32_t rep = static_cast<int32_t>(s) & (p.G.reps - 1);
+    for_each_piece(r, p.G, [&](int32_t b, int32_t, int32_t len) { atomicAdd(p.brick_count + piece_slot(p.G, b, len, rep), 1); });
 }
 
 // One segment per thread.
@@ -187,14 +220,14 @@ __global__ void __launch_bounds__(256) k_bin_scatter(BinParams p)
     const int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (s >= p.n || ld_volatile_i32(p.status) != 0) return;
     if (__ldg(p.brick_off + p.G.n_slots) > p.capacity) return;  // the volume falls back to atomics
-    const int32_t rep = static_cast<int32_t>(s % p.G.reps);
+    const int32_t rep = static_cast<int32_t>(s) & (p.G.reps - 1);
     int32_t r[6];
     load_record(p.segs, s, r);
     if (!endpoints_inside(r, p.G)) return;
     // slot reservations of up to four pieces are in flight together before
     // their stores, so the returning atomics' latency overlaps
     constexpr int kBatch = 4;
-    int64_t bb[kBatch];
+    uint32_t bb[kBatch];
     uint64_t val[kBatch];
     int nb = 0;
     auto flush = [&]() {
@@ -207,7 +240,7 @@ __global__ void __launch_bounds__(256) k_bin_scatter(BinParams p)
             if (e < nb) p.pieces[pos[e]] = val[e];
         nb = 0;
     };
-    for_each_piece(r, p.G, [&](int64_t b, int32_t k, int32_t len) {
+    for_each_piece(r, p.G, [&](int32_t b, int32_t k, int32_t len) {
 #pragma unroll
         for (int e = 0; e < kBatch; ++e)
             if (e == nb) {
@@ -228,7 +261,8 @@ struct BrickParams {
     uint32_t *mask;
     const int32_t *status;
     uint32_t *ticket;  // zeroed before launch
-    int32_t use_tma;   // merge by one TMA tensor reduce-OR per brick (tensor map valid)
+    int32_t use_tma;   // merge by one TMA tensor reduce-OR (or store) per brick (tensor map valid)
+    int32_t fresh;     // write every brick (zeros included) instead of OR-ing into the volume
 };
 
 // TMA tensor reduction of a whole brick tile from shared memory into the volume:
@@ -246,42 +280,58 @@ __device__ __forceinline__ void tma_reduce_or_3d(const CUtensorMap *tmap, const 
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
 
+// TMA tensor store of a whole brick tile (the volume's previous content there is
+// replaced); parts of the box outside the volume are skipped by the hardware.
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *tmap, const void *smem, int32_t x, int32_t y, int32_t z)
+{
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                     reinterpret_cast<uint64_t>(tmap)),
+                 "r"(x), "r"(y), "r"(z), "r"(smem_addr(smem))
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
 __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // Merge a brick's shared bitmap into the volume. Brick row (ly, lz) holds bxw
 // words that are contiguous in the volume; a warp covers 32 consecutive words.
-// Only touched words are read and written. Eight independent loads per thread
-// are issued before the stores, so DRAM latency is paid once per group, not
-// once per word. The brick owns its words: plain loads and stores suffice.
+// OR mode reads and writes only touched words; fresh mode writes every word of
+// the brick inside the volume (zeros included) and reads none. Eight
+// independent loads per thread are issued before the stores, so DRAM latency is
+// paid once per group, not once per word. The brick owns its words: plain
+// loads and stores suffice.
 __device__ __forceinline__ void merge_brick(const uint32_t *bits, const BrickGeom &G, int32_t X0, int32_t Y0,
-                                            int32_t Z0, uint32_t *mask)
+                                            int32_t Z0, uint32_t *mask, bool fresh)
 {
     constexpr int kGroup = 8;
     const int t = threadIdx.x;
     for (int q0 = 0; q0 < G.words; q0 += kGroup * kBrickThreads) {
         uint32_t v[kGroup], old[kGroup];
         int64_t gw[kGroup];
+        bool wr[kGroup];
 #pragma unroll
         for (int e = 0; e < kGroup; ++e) {
             const int q = q0 + e * kBrickThreads + t;
             v[e] = 0;
             gw[e] = 0;
+            wr[e] = false;
             if (q < G.words) {
                 const uint32_t b = bits[q];
                 const int32_t row = q >> G.log_bxw, col = q & (G.bxw - 1);
                 const int32_t y = Y0 + (row & (G.B[1] - 1)), z = Z0 + (row >> G.log_b1);
-                if (b != 0 && y < G.dim[1] && z < G.dim[2] && X0 / 32 + col < G.row_words) {
+                if ((fresh || b != 0) && y < G.dim[1] && z < G.dim[2] && X0 / 32 + col < G.row_words) {
                     v[e] = b;
+                    wr[e] = true;
                     gw[e] = X0 / 32 + col + static_cast<int64_t>(G.row_words) * (y + static_cast<int64_t>(G.dim[1]) * z);
                 }
             }
         }
 #pragma unroll
-        for (int e = 0; e < kGroup; ++e) old[e] = v[e] ? mask[gw[e]] : 0u;
+        for (int e = 0; e < kGroup; ++e) old[e] = (wr[e] && !fresh) ? mask[gw[e]] : 0u;
 #pragma unroll
         for (int e = 0; e < kGroup; ++e)
-            if (v[e]) mask[gw[e]] = old[e] | v[e];
+            if (wr[e]) mask[gw[e]] = old[e] | v[e];
     }
 }
 
@@ -307,7 +357,10 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
     const int t = threadIdx.x;
     const int lane = t & 31;
     if (ld_volatile_i32(p.status) != 0) return;
-    if (__ldg(p.brick_off + p.G.n_slots) > p.capacity) return;  // pieces did not fit: atomics path
+    // pieces that did not fit: the gated atomics pass ORs the voxels in (after a
+    // fresh volume has been cleared here, brick by brick)
+    const bool overflow = __ldg(p.brick_off + p.G.n_slots) > p.capacity;
+    if (overflow && !p.fresh) return;
     const BrickGeom &G = p.G;
     const int64_t slots_per_brick = static_cast<int64_t>(kPieceClasses) * G.reps;
     const uint32_t bw = static_cast<uint32_t>(G.B[0]);
@@ -328,9 +381,9 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
         const int64_t b = sm.brick;
         const int32_t X0 = sm.origin[0], Y0 = sm.origin[1], Z0 = sm.origin[2];
         if (b >= G.n_bricks) break;
-        const int64_t lo = __ldg(p.brick_off + b * slots_per_brick);
-        const int64_t hi = __ldg(p.brick_off + (b + 1) * slots_per_brick);
-        if (lo == hi) {
+        const int64_t lo = overflow ? 0 : __ldg(p.brick_off + b * slots_per_brick);
+        const int64_t hi = overflow ? 0 : __ldg(p.brick_off + (b + 1) * slots_per_brick);
+        if (lo == hi && !p.fresh) {
             __syncthreads();  // everyone has read the ticket slot before it is rewritten
             continue;
         }
@@ -381,10 +434,11 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
         if (p.use_tma) {
             if (t == 0) {
                 fence_proxy_async_smem();  // the bitmap's generic writes, visible to the TMA unit
-                tma_reduce_or_3d(&tmap, sm.bits, X0 / 32, Y0, Z0);
+                if (p.fresh) tma_store_3d(&tmap, sm.bits, X0 / 32, Y0, Z0);
+                else tma_reduce_or_3d(&tmap, sm.bits, X0 / 32, Y0, Z0);
             }
         } else {
-            merge_brick(sm.bits, G, X0, Y0, Z0, p.mask);
+            merge_brick(sm.bits, G, X0, Y0, Z0, p.mask, p.fresh != 0);
             __syncthreads();
         }
     }

@@ -554,6 +554,28 @@ __global__ void __launch_bounds__(256) k_scene_map(const SceneDesc *scenes, int3
     for (int64_t i = threadIdx.x; i < sd.n; i += blockDim.x) scene_of[sd.seg_begin + i] = k;
 }
 
+// Fresh batched volumes: scene blockIdx.y's volume zeroed by kSceneClearCtas
+// CTAs (16-byte stores from the first 16-byte boundary on), after k_scene_map
+// has checked the table (nothing written otherwise).
+constexpr unsigned kSceneClearCtas = 512;
+__global__ void __launch_bounds__(256) k_scene_clear(const SceneDesc *scenes, const int32_t *status)
+{
+    if (ld_volatile_i32(status) != 0) return;
+    const SceneDesc sd = scenes[blockIdx.y];
+    if (sd.mask == nullptr) return;
+    const int64_t words = (static_cast<int64_t>(sd.w) * sd.h * sd.d + 31) / 32;
+    const int64_t tid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t nthreads = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    // words before the first 16-byte boundary, then whole 16-byte groups, then the tail
+    const int64_t head = min64(words, static_cast<int64_t>((16 - (reinterpret_cast<uintptr_t>(sd.mask) & 15)) & 15) / 4);
+    if (tid < head) sd.mask[tid] = 0u;
+    uint4 *body = reinterpret_cast<uint4 *>(sd.mask + head);
+    const int64_t groups = (words - head) / 4;
+    for (int64_t i = tid; i < groups; i += nthreads) body[i] = make_uint4(0u, 0u, 0u, 0u);
+    const int64_t tail0 = head + 4 * groups;
+    if (tail0 + tid < words) sd.mask[tail0 + tid] = 0u;
+}
+
 // First global voxel id of every scene (and V at index n_scenes).
 __global__ void k_scene_base(const SceneDesc *scenes, int32_t n_scenes, const int64_t *offsets, int64_t n_total,
                              int64_t *base, int64_t *base_out, const int32_t *status)

@@ -214,9 +214,10 @@ class _Handle:
 
 
 class GpuLauncher:
-    """Launches a batch with vox_generate_batched (volumes only) on one of
-    ``slots`` streams: segments copied from pinned host memory, fresh zeroed
-    volumes, one scene table, one workspace, one completion event."""
+    """Launches a batch with vox_generate_batched (volumes only, VOX_OUT_FRESH)
+    on one of ``slots`` streams: segments copied from pinned host memory, new
+    volumes cleared by the launch, one scene table, one workspace, one
+    completion event."""
 
     def __init__(self, slots: int, device="cuda", keep_results: bool = False):
         import torch
@@ -239,7 +240,8 @@ class GpuLauncher:
                 if r.n:
                     segs[off:off + r.n].copy_(r.segs_host, non_blocking=True)
                 off += r.n
-            masks = [torch.zeros((r.mask_bytes // 4,), dtype=torch.int32, device=self.device) for r in reqs]
+            # fresh volumes: cleared by the batched launch (one kernel), not one fill per request
+            masks = [torch.empty((r.mask_bytes // 4,), dtype=torch.int32, device=self.device) for r in reqs]
             table = batching.scene_table_bytes([r.n for r in reqs], [r.dims for r in reqs],
                                                [m.data_ptr() for m in masks])
             scenes = torch.frombuffer(bytearray(table), dtype=torch.uint8).pin_memory().to(self.device,
@@ -248,7 +250,7 @@ class GpuLauncher:
                              device=self.device)
             status = torch.zeros(1, dtype=torch.int32, device=self.device)
             st = vox.load().vox_generate_batched(
-                vox._ptr(segs), n_total, vox._ptr(scenes), len(reqs), None, 0, vox.OUT_BITMASK, None,
+                vox._ptr(segs), n_total, vox._ptr(scenes), len(reqs), None, 0, vox.OUT_BITMASK | vox.OUT_FRESH, None,
                 vox._ptr(ws), ws.numel(), vox._ptr(status), vox._stream(stream))
             if st != vox.OK:
                 raise vox.VoxError(st, "vox_generate_batched")

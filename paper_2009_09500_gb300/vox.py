@@ -32,6 +32,7 @@ ERR_ALIGNMENT = 8
 OUT_LIST32 = 1
 OUT_LIST64 = 2
 OUT_BITMASK = 4
+OUT_FRESH = 8
 
 EXPORTED = (
     "vox_workspace_size", "vox_count", "vox_generate", "vox_generate_from_scan",

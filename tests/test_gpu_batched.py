@@ -38,6 +38,8 @@ def check_scenes(batch, scenes, sample=None):
             want = O.list64(w.segs) if batch.flags & vox.OUT_LIST64 else O.list32(w.segs)
             assert np.array_equal(got.view(want.dtype), want), f"scene {k} list"
         if batch.masks:
+            if batch.masks[k] is None:
+                continue
             got = batch.masks[k].cpu().numpy().view(np.uint32)
             assert np.array_equal(got, O.bitmask(w.segs, w.dims)), f"scene {k} volume"
 
@@ -136,3 +138,26 @@ def test_batched_list32_rejects_wide_scene():
     b.run()
     torch.cuda.synchronize()
     assert int(b.status.item()) == vox.ERR_PACK_WIDTH
+
+
+def test_batched_fresh_volumes_overwrite_stale_bits():
+    """VOX_OUT_FRESH: every scene's volume is cleared on the device first, so
+    stale bits vanish; a scene without a volume is skipped."""
+    scenes = small_scenes(10, seed=44)
+    b = batching.make_batch(scenes, flags=vox.OUT_LIST32 | vox.OUT_BITMASK | vox.OUT_FRESH)
+    for m in b.masks:
+        m.fill_(-1)
+    b.run()
+    check_scenes(b, scenes)
+    # drop scene 3's volume from the table: its (stale) buffer stays as it is
+    ptrs = [m.data_ptr() for m in b.masks]
+    ptrs[3] = 0
+    table = batching.scene_table_bytes(b.seg_counts, b.dims, ptrs)
+    b.scenes.copy_(torch.frombuffer(bytearray(table), dtype=torch.uint8))
+    for m in b.masks:
+        m.fill_(-1)
+    b.run()
+    torch.cuda.synchronize()
+    assert bool((b.masks[3] == -1).all())
+    b.masks[3] = None
+    check_scenes(b, scenes)

@@ -16,7 +16,7 @@ from paper_2009_09500_gb300 import vox, workloads
 
 pytestmark = pytest.mark.gpu
 
-L32, L64, BM = vox.OUT_LIST32, vox.OUT_LIST64, vox.OUT_BITMASK
+L32, L64, BM, FR = vox.OUT_LIST32, vox.OUT_LIST64, vox.OUT_BITMASK, vox.OUT_FRESH
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -40,7 +40,8 @@ def full_check(segs, dims, flags, **kw):
     if flags & (L32 | L64):
         assert_list_equal(r["list_full"], oracle_list(O, segs, flags), r["V"])
     if flags & BM:
-        want = O.bitmask(segs, dims, None if kw.get("mask_init") is None else kw["mask_init"].copy())
+        fresh = (flags & FR) or kw.get("mask_init") is None
+        want = O.bitmask(segs, dims, None if fresh else kw["mask_init"].copy())
         assert np.array_equal(r["mask"], want), f"{int((r['mask'] != want).sum())} volume words differ"
     return r
 
@@ -456,3 +457,72 @@ def test_bricks_generation_repeated_after_one_count():
         torch.cuda.synchronize()
         assert int(status.item()) == 0
         assert np.array_equal(mask.cpu().numpy().view(np.uint32), want)
+
+
+# ------------------------------------------- fresh volumes (VOX_OUT_FRESH): overwritten
+def garbage_mask(rng, dims):
+    return rng.integers(0, 2**32, size=vox.vox_mask_words(dims), dtype=np.uint64).astype(np.uint32)
+
+
+@pytest.mark.parametrize("dims,pieces", [
+    ((256, 256, 256), "plan"),   # bricks, TMA tensor store
+    ((128, 128, 64), "plan"),    # bricks, TMA, B0 = 128
+    ((96, 40, 17), "plan"),      # bricks, plain-store merge (B0 = 64), edge bricks
+    ((32, 7, 5), "plan"),        # one ragged brick
+    ((13, 7, 5), "plan"),        # w % 32 != 0: cleared, then atomics
+    ((64, 64, 64), None),        # plain workspace: cleared, then atomics
+    ((256, 256, 256), 100),      # pieces do not fit: bricks cleared, gated atomics
+])
+def test_fresh_volume_overwrites(dims, pieces):
+    rng = np.random.default_rng(sum(dims) + (7 if pieces is None else 0))
+    segs = workloads.uniform_segments(rng, 3000, dims)
+    full_check(segs, dims, BM | FR, pieces=pieces, mask_init=garbage_mask(rng, dims))
+    full_check(segs, dims, L32 | BM | FR, pieces=pieces, mask_init=garbage_mask(rng, dims), use_from_scan=True)
+
+
+def test_fresh_volume_with_no_segments_is_cleared():
+    dims = (64, 32, 16)
+    rng = np.random.default_rng(71)
+    r = run_gpu(np.zeros((0, 6), np.int32), dims, BM | FR, mask_init=garbage_mask(rng, dims))
+    assert r["status"] == 0 and (r["mask"] == 0).all()
+
+
+def test_fresh_volume_atomic_tuning():
+    rng = np.random.default_rng(72)
+    dims = (256, 128, 64)
+    segs = workloads.uniform_segments(rng, 4000, dims)
+    vox.vox_set_tuning(0, vox.VOLUME_ATOMIC, 0)
+    try:
+        full_check(segs, dims, L32 | BM | FR, pieces="plan", mask_init=garbage_mask(rng, dims))
+    finally:
+        vox.vox_set_tuning(0, 0, 0)
+
+
+def test_fresh_config2_full_size():
+    """The benchmarked call: list32 and a fresh brick-built volume over a volume
+    full of stale bits, whole outputs compared."""
+    w = workloads.config2()
+    rng = np.random.default_rng(73)
+    full_check(w.segs, w.dims, L32 | BM | FR, pieces="plan", mask_init=garbage_mask(rng, w.dims),
+               use_from_scan=True)
+
+
+def test_fresh_device_error_leaves_volume_unchanged_or_cleared():
+    w = workloads.config1()
+    segs = w.segs.copy()
+    segs[99, 2] = 300  # z0 outside [0, 256)
+    rng = np.random.default_rng(74)
+    init = garbage_mask(rng, w.dims)
+    r = run_gpu(segs, w.dims, BM | FR, mask_init=init)
+    assert r["status"] == vox.ERR_OUT_OF_BOUNDS
+    assert (r["mask"] == init).all() or (r["mask"] == 0).all()
+
+
+def test_fresh_without_bitmask_is_rejected():
+    segs = torch.zeros((4, 6), dtype=torch.int32, device="cuda")
+    ws = torch.empty(vox.vox_workspace_size(4), dtype=torch.uint8, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    lst = torch.empty(16, dtype=torch.int32, device="cuda")
+    with pytest.raises(vox.VoxError) as e:
+        vox.vox_generate(segs, (8, 8, 8), ws, st, lst, flags=L32 | FR)
+    assert e.value.status == vox.ERR_INVALID_ARG
