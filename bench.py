@@ -272,6 +272,82 @@ def measure_batched(steps: int, dev) -> dict:
     }
 
 
+# The paper's GTX 1070 Ti column (ms) of Tables 2, 3 and 4: context only (other
+# hardware; its timings were taken with a profiler and include its own copies).
+PAPER_E1_MS = (0.45, 0.46, 0.49, 0.51, 0.52, 0.67, 0.92, 1.52, 2.22, 3.65428571)
+PAPER_E2_MS = (0.42, 0.46, 0.75, 1.44, 4.13, 10.91, 21.70, 43.85, 105.84, 218.17, 427.62)
+PAPER_E3_MS = 4071.01
+
+
+def measure_sweeps(dev, reps: int = 5, e2e: bool = True) -> dict:
+    """The three sweeps of Section 5 (Tables 2-4) with 64-bit lists in a 2^21-edge
+    volume: E1 one segment of 10^3..10^6 voxels; E2 1024 segments of equal length
+    20..200 000 voxels; E3 1024 segments of pairwise different lengths totalling
+    10^9 voxels. Each point times one vox_generate call (count + scan + list) on
+    device buffers (L2 flushed between calls, CUDA events) and, end to end, one
+    vox_generate_host call (pinned host segments in, host list out)."""
+    import torch
+
+    from paper_2009_09500_gb300 import vox, workloads
+
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    flags = vox.OUT_LIST64
+
+    def point(w, paper_ms):
+        n = w.n
+        d = np.abs(w.segs[:, 3:].astype(np.int64) - w.segs[:, :3])
+        V = int((d.max(axis=1) + 1).sum())
+        segs = torch.from_numpy(w.segs).to(dev)
+        ws = torch.empty(vox.vox_workspace_size(n), dtype=torch.uint8, device=dev)
+        status = torch.zeros(1, dtype=torch.int32, device=dev)
+        lst = torch.empty(V, dtype=torch.int64, device=dev)
+        ts = []
+        for i in range(reps + 2):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            vox.vox_generate(segs, w.dims, ws, status, lst, None, flags, stream, capacity=V)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if i >= 2:
+                ts.append(a.elapsed_time(b))
+        if int(status.item()) != 0:
+            raise RuntimeError(f"device status {vox.strerror(int(status.item()))}")
+        ms = float(np.median(ts))
+        out = {"segments": n, "voxels": V, "device_ms": ms, "voxels_per_s": V / ms * 1e3,
+               "paper_gtx1070ti_ms": paper_ms}
+        del segs, ws, lst
+        if e2e:
+            h_segs = torch.from_numpy(w.segs).pin_memory()
+            h_list = torch.empty(V, dtype=torch.int64).pin_memory()
+            arena = torch.empty(vox.vox_host_arena_size(n, w.dims, flags, V), dtype=torch.uint8, device=dev)
+            te = []
+            for i in range(reps + 1):
+                torch.cuda.synchronize()
+                ta = time.perf_counter()
+                got = vox.vox_generate_host(h_segs, w.dims, arena, h_list, None, flags, stream)
+                if i >= 1:
+                    te.append(time.perf_counter() - ta)
+                assert got == V
+            out.update({"e2e_ms": 1000 * float(np.median(te)), "h2d_bytes": 24 * n, "d2h_bytes": 8 * V})
+            del h_list, arena
+        torch.cuda.empty_cache()
+        return out
+
+    e1 = [dict(length=L, **point(workloads.sweep_single(L), p))
+          for L, p in zip(workloads.E1_LENGTHS, PAPER_E1_MS)]
+    e2 = [dict(length=L, **point(workloads.sweep_fixed(L), p))
+          for L, p in zip(workloads.E2_LENGTHS, PAPER_E2_MS)]
+    e3 = point(workloads.sweep_giga(), PAPER_E3_MS)
+    return {"E1_single_segment": e1, "E2_1024_equal_length": e2, "E3_1024_arbitrary_total_1e9": e3,
+            "output": "list64 (x | y << 21 | z << 42), 2^21-edge volume",
+            "device_ms": "one vox_generate call (count + scan + list), median of "
+                         f"{reps}, L2 flushed between calls",
+            "e2e_ms": "one vox_generate_host call (pinned H2D of the segments, count, list, D2H of the "
+                      "list), median, synchronous"}
+
+
 def measure_serving(duration_s: float, dev) -> dict:
     """The request stream: Poisson arrivals at 2000 req/s for `duration_s`,
     each request a scene of log-uniform 1e3..1e6 segments in a 128^3..1024^3
@@ -438,6 +514,9 @@ def run_ours(args):
     served = None
     if not args.no_serve and world == 1:
         served = measure_serving(args.serve_seconds, dev)
+    sweeps = None
+    if not args.no_sweeps and world == 1:
+        sweeps = measure_sweeps(dev)
 
     if rank != 0:
         return 0
@@ -461,7 +540,7 @@ def run_ours(args):
         "kernels_ms": {"count_scan": float(np.mean(scan_ms)), "list": list_mean, "volume": vol_mean},
         "wall_s_timed_region": wall,
         "roofline": roofline, "roofline_other": roofline_other, "cpu_baseline": cpu, "e2e": e2e,
-        "batched_vs_plain": batched, "serving": served,
+        "batched_vs_plain": batched, "serving": served, "sweeps": sweeps,
         "clocks": clocks,
         "gpu_launches": 7 * args.steps,
         "gpu_launches_note": "per step: k_scan<true>, k_generate (list), k_bin_count, k_scan<false>, "
@@ -484,6 +563,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-sweeps", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()

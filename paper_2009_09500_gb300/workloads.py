@@ -167,3 +167,42 @@ def sweep_single(n_voxels: int, seed: int = 5, edge: int = 1 << 21) -> Workload:
     rng = np.random.default_rng(seed)
     segs = _segments_from_major(rng, np.array([n_voxels - 1], dtype=np.int64), edge)
     return Workload(f"single-{n_voxels}vox", segs, (edge,) * 3)
+
+
+# Lengths of the three sweeps of Section 5 (Tables 2-4), in voxels.
+E1_LENGTHS = (1000, 2000, 5000, 10000, 20000, 50000, 100000, 200000, 500000, 1000000)
+E2_LENGTHS = (20, 50, 100, 1000, 2000, 5000, 10000, 20000, 50000, 100000, 200000)
+E3_TOTAL = 10**9
+
+
+def sweep_fixed(length: int, n: int = 1024, seed: int = 6, edge: int = 1 << 21) -> Workload:
+    """Table 3 sweep point: n segments of `length` voxels each (major |delta| =
+    length - 1), random directions, inside an edge^3 volume."""
+    rng = np.random.default_rng(seed + length)
+    segs = _segments_from_major(rng, np.full(n, length - 1, dtype=np.int64), edge)
+    return Workload(f"fixed-{n}x{length}vox", segs, (edge,) * 3)
+
+
+def giga_lengths(rng: np.random.Generator, n: int, total: int, edge: int) -> np.ndarray:
+    """n pairwise different segment lengths (voxels) summing to exactly `total`,
+    each at most edge: weights uniform in [0.1, 1) scaled to the total, the
+    rounding remainder spread one voxel at a time over the longest segments."""
+    if total < n * (n + 1) // 2 or total > n * edge:
+        raise ValueError("total out of reach")
+    while True:
+        wts = rng.uniform(0.1, 1.0, size=n)
+        lengths = np.floor(wts / wts.sum() * total).astype(np.int64)
+        rest = total - int(lengths.sum())
+        order = np.argsort(-lengths, kind="stable")
+        lengths[order[:rest]] += 1
+        if len(np.unique(lengths)) == n and lengths.min() >= 1 and lengths.max() <= edge:
+            return lengths
+
+
+def sweep_giga(total: int = E3_TOTAL, n: int = 1024, seed: int = 7, edge: int = 1 << 21) -> Workload:
+    """Table 4 shape: n segments of pairwise different, arbitrary lengths whose
+    voxel counts sum to `total` (one giga-voxel by default)."""
+    rng = np.random.default_rng(seed)
+    lengths = giga_lengths(rng, n, total, edge)
+    segs = _segments_from_major(rng, lengths - 1, edge)
+    return Workload(f"arbitrary-{n}seg-{total}vox", segs, (edge,) * 3)
