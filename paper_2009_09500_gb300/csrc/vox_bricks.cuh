@@ -4,12 +4,13 @@
 // read-modify-write of a 32-byte sector per voxel (the volume is far larger than
 // L2 for big scenes), which makes the volume store DRAM-bound at a small fraction
 // of the bandwidth. Instead the volume is cut into bricks of whole 32-bit words
-// (B0 x B1 x B2 voxels, B0 a multiple of 32, at most 8192 words), every segment
+// (B0 x B1 x B2 voxels, B0 a multiple of 32, at most 16384 words), every segment
 // is cut into pieces that stay inside one brick, the pieces are counting-sorted
 // by brick, and one CTA owns each brick: it ORs the brick's voxels into a
-// shared-memory bitmap and merges the bitmap into the volume with one coalesced
-// read-modify-write per touched word. Each volume sector then crosses DRAM at
-// most twice (read + write), whatever the number of voxels in it.
+// shared-memory bitmap and merges the bitmap into the volume in one pass (a TMA
+// tensor reduce-OR, or a store of the whole brick for a fresh volume). Each
+// volume sector then crosses DRAM at most twice (read + write), whatever the
+// number of voxels in it.
 //
 //   k_bin_count    pieces per brick (one thread per segment, global atomics)
 //   k_scan<false>  exclusive scan of the per-brick counts (decoupled look-back)
