@@ -4,7 +4,7 @@
 // read-modify-write of a 32-byte sector per voxel (the volume is far larger than
 // L2 for big scenes), which makes the volume store DRAM-bound at a small fraction
 // of the bandwidth. Instead the volume is cut into bricks of whole 32-bit words
-// (B0 x B1 x B2 voxels, B0 a multiple of 32, at most 16384 words), every segment
+// (B0 x B1 x B2 voxels, B0 a multiple of 32, at most 32768 words), every segment
 // is cut into pieces that stay inside one brick, the pieces are counting-sorted
 // by brick, and one CTA owns each brick: it ORs the brick's voxels into a
 // shared-memory bitmap and merges the bitmap into the volume in one pass (a TMA
@@ -31,8 +31,8 @@
 
 namespace vox {
 
-constexpr int kBrickThreads = 512;
-constexpr int kBrickWordsMax = 16384;  // 64 KB shared bitmap per brick
+constexpr int kBrickThreads = 1024;  // one CTA per SM (the bitmap takes 128 KB)
+constexpr int kBrickWordsMax = 32768;  // 128 KB shared bitmap per brick
 constexpr int32_t kNoStep = 0x7fffffff;
 
 struct BrickGeom {
@@ -392,7 +392,10 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
             if (t == 0) bulk_wait_read_all();
         }
         __syncthreads();
-        for (int q = t; q < G.words; q += kBrickThreads) sm.bits[q] = 0u;
+        {  // words is a multiple of 4 (bxw * B1 * B2 with B1 * B2 >= 8)
+            uint4 *z = reinterpret_cast<uint4 *>(sm.bits);
+            for (int q = t; q < G.words / 4; q += kBrickThreads) z[q] = make_uint4(0u, 0u, 0u, 0u);
+        }
         __syncthreads();
         // brick-local bit index of (x, y, z): (x - X0) + B0 (y - Y0) + B0 B1 (z - Z0),
         // kept modulo 2^32 while stepping (only the local value is ever used)

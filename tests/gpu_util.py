@@ -117,12 +117,12 @@ def brick_pieces_expected(O, segs, dims):
     """Number of brick pieces (maximal runs of a segment's voxels inside one
     brick) from the oracle's voxels and the documented brick shape: B0 = the
     largest 32 * 2^k not above min(w, 256), then the largest power-of-two rows
-    B1 x B2 (B1 = 2 B2 or B2) with B0/32 * B1 * B2 <= 16384 words."""
+    B1 x B2 (B1 = 2 B2 or B2) with B0/32 * B1 * B2 <= 32768 words."""
     w = int(dims[0])
     b0 = 32
     while 2 * b0 <= min(w, 256):
         b0 *= 2
-    rows = 16384 // (b0 // 32)
+    rows = 32768 // (b0 // 32)
     p2 = 1
     while (2 * p2) ** 2 <= rows:
         p2 *= 2
