@@ -448,12 +448,15 @@ def run_ours(args):
         step(evs[k])
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
-    # the same step captured once as a CUDA graph and replayed: the kernels are the
-    # same launches; the graph removes the launch gaps and the small memsets'
-    # overhead between them. This is the step the headline value times.
+    # the same step as batching.SceneStep: captured once as a CUDA graph, the list
+    # and the volume on two streams after the count (the same launches; the graph
+    # removes the launch gaps, the two streams let the list kernel and the
+    # volume's binning overlap). This is the step the headline value times.
     from paper_2009_09500_gb300 import batching
 
-    graph = batching.GraphRunner(lambda s: step(None, s))
+    graph = batching.SceneStep(segs, w.dims, vox.OUT_LIST32, volume=True, device=dev)
+    if (graph.V, graph.P) != (V, P):
+        raise RuntimeError("plan mismatch")
     for _ in range(args.warmup):
         flush.zero_()
         graph.replay()
@@ -470,9 +473,12 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop()
-    st = int(status.item())
-    if st != 0:
-        raise RuntimeError(f"device status {vox.strerror(st)}")
+    for st in (int(status.item()), int(graph.status.item())):
+        if st != 0:
+            raise RuntimeError(f"device status {vox.strerror(st)}")
+    # the graph's outputs are the eager step's, word for word
+    if not (torch.equal(graph.lst, lst) and torch.equal(graph.mask, mask)):
+        raise RuntimeError("graph step and eager step disagree")
     eager_ms = [e[0].elapsed_time(e[3]) for e in evs]
     step_ms = [g[0].elapsed_time(g[1]) for g in gevs]
     scan_ms = [e[0].elapsed_time(e[1]) for e in evs]
@@ -552,8 +558,9 @@ def run_ours(args):
                    "volume_path": "per-voxel atomics" if tuning and tuning["params"]["volume_path"] == 1
                    else "brick ownership", "pieces": P,
                    "tuning": tuning,
-                   "launch": "the step's launches captured once as a CUDA graph and replayed on one stream; "
-                             "per-phase times from the same launches issued eagerly with events between phases",
+                   "launch": "batching.SceneStep: the step's launches captured once as a CUDA graph (count, then "
+                             "list and volume on two streams) and replayed; per-phase times from the same launches "
+                             "issued eagerly on one stream with events between phases",
                    "l2": "flushed between steps by a 256 MiB write (outside the step events)",
                    "parallelism": f"replicas x{world} (independent batches)"},
         "segments_per_s": n * world / (ms_mean_max / 1000.0),

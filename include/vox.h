@@ -132,9 +132,13 @@ vox_status vox_generate(const vox_segment *d_segs, int64_t n, vox_dims dims,
 /*
  * vox_generate_from_scan -- the generation step alone, reusing the counts and
  * offsets that a preceding vox_count left in d_ws for the same d_segs, n and
- * dims, on the same stream. Does not reset *d_status: an error found by that
- * vox_count keeps this call from writing anything. Arguments as for
- * vox_generate.
+ * dims, on the same stream (or on a stream ordered after it). Does not reset
+ * *d_status: an error found by that vox_count keeps this call from writing
+ * anything. Arguments as for vox_generate.
+ * After one vox_count, a list-only call (VOX_OUT_LIST32/64) and a volume-only
+ * call (VOX_OUT_BITMASK) may run concurrently on two streams: the list reads
+ * the scanned offsets, the volume reads them and writes only the brick arrays
+ * that follow them in the workspace, and errors are recorded first-wins.
  */
 vox_status vox_generate_from_scan(const vox_segment *d_segs, int64_t n, vox_dims dims,
                                   void *d_list, int64_t list_capacity, uint32_t *d_mask,

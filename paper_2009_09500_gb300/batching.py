@@ -167,3 +167,62 @@ class PlainScenes:
             if s.shape[0] == 0:
                 continue
             vox.vox_generate(s, dims, ws, b.status, lst, mask, b.flags, stream, capacity=V)
+
+
+class SceneStep:
+    """One scene's whole step -- count + scan, the list, a fresh volume -- on
+    resident device buffers, captured once as a CUDA graph. After the count the
+    list and the volume are issued on two streams: the two calls share only
+    read-only parts of the workspace (the segments and the scanned offsets), so
+    the list kernel and the volume's binning overlap on the device.
+
+    segs: int32 [n, 6] on the device; list_flag: vox.OUT_LIST32, vox.OUT_LIST64
+    or 0 (no list); volume: build the occupancy volume too."""
+
+    def __init__(self, segs, dims, list_flag=vox.OUT_LIST32, volume=True, device="cuda"):
+        import torch
+
+        self.segs = segs
+        self.dims = tuple(int(v) for v in dims)
+        self.list_flag = int(list_flag)
+        self.volume = bool(volume)
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)
+        n = int(segs.shape[0])
+        ws = torch.empty(vox.vox_workspace_size_volume(n, self.dims, 0), dtype=torch.uint8, device=device)
+        self.V, self.P = vox.vox_plan(segs, self.dims, ws, self.status) if n else (0, 0)
+        self.ws = torch.empty(vox.vox_workspace_size_volume(n, self.dims, self.P), dtype=torch.uint8, device=device)
+        self.lst = None
+        if self.list_flag:
+            dt = torch.int64 if self.list_flag == vox.OUT_LIST64 else torch.int32
+            self.lst = torch.empty(max(self.V, 1), dtype=dt, device=device)
+        self.mask = torch.empty(vox.vox_mask_words(self.dims), dtype=torch.int32, device=device) if volume else None
+        self.side = torch.cuda.Stream(device=device)
+        self.graph = GraphRunner(self.launch)
+
+    def launch(self, s):
+        """Enqueue the step on stream `s` (the list on a second stream, joined back)."""
+        import torch
+
+        vox.vox_count(self.segs, self.dims, self.ws, self.status, None, None, s)
+        if self.segs.shape[0] == 0:
+            if self.volume:
+                vox.vox_generate_from_scan(self.segs, self.dims, self.ws, self.status, None, self.mask,
+                                           vox.OUT_BITMASK | vox.OUT_FRESH, s)
+            return
+        counted = torch.cuda.Event()
+        counted.record(s)
+        if self.list_flag:
+            self.side.wait_event(counted)
+            vox.vox_generate_from_scan(self.segs, self.dims, self.ws, self.status, self.lst, None, self.list_flag,
+                                       self.side, capacity=self.V)
+        if self.volume:
+            vox.vox_generate_from_scan(self.segs, self.dims, self.ws, self.status, None, self.mask,
+                                       vox.OUT_BITMASK | vox.OUT_FRESH, s)
+        if self.list_flag:
+            listed = torch.cuda.Event()
+            listed.record(self.side)
+            s.wait_event(listed)
+
+    def replay(self):
+        """Replay the captured step on the current stream (asynchronous)."""
+        self.graph.replay()

@@ -161,3 +161,37 @@ def test_batched_fresh_volumes_overwrite_stale_bits():
     assert bool((b.masks[3] == -1).all())
     b.masks[3] = None
     check_scenes(b, scenes)
+
+
+@pytest.mark.parametrize("which", ["config1", "config2"])
+def test_scene_step_graph_matches_oracle(which):
+    """batching.SceneStep (count, then list and fresh volume on two streams, one
+    CUDA graph), replayed twice over stale outputs: list and volume against the
+    oracle, whole."""
+    O = get_oracle()
+    w = getattr(workloads, which)()
+    segs = torch.from_numpy(w.segs).cuda()
+    st = batching.SceneStep(segs, w.dims, vox.OUT_LIST32, volume=True)
+    for _ in range(2):
+        st.lst.fill_(-1)
+        st.mask.fill_(-1)
+        st.replay()
+        torch.cuda.synchronize()
+        assert int(st.status.item()) == 0
+        assert np.array_equal(st.lst.cpu().numpy().view(np.uint32), O.list32(w.segs))
+        assert np.array_equal(st.mask.cpu().numpy().view(np.uint32), O.bitmask(w.segs, w.dims))
+
+
+def test_scene_step_list64_only_and_empty():
+    O = get_oracle()
+    w = workloads.config1()
+    segs = torch.from_numpy(w.segs).cuda()
+    st = batching.SceneStep(segs, w.dims, vox.OUT_LIST64, volume=False)
+    st.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(st.lst.cpu().numpy().view(np.uint64), O.list64(w.segs))
+    empty = batching.SceneStep(torch.zeros((0, 6), dtype=torch.int32, device="cuda"), (64, 64, 64), 0, volume=True)
+    empty.mask.fill_(-1)
+    empty.replay()
+    torch.cuda.synchronize()
+    assert int(empty.status.item()) == 0 and bool((empty.mask == 0).all())
