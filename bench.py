@@ -65,19 +65,23 @@ def _kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def _recorded_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from a committed ncu summary, if it was
-    taken on the current kernel sources (else None)."""
+def _recorded_traffic(kernels):
+    """DRAM bytes per launch (summed over `kernels`, one launch each) from the
+    committed ncu record, if every entry was taken on the current kernel sources
+    (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
     except (OSError, ValueError):
         return None
-    ent = rec.get(kernel)
-    if not ent or ent.get("source_hash") != _kernel_source_hash():
-        return None
-    return ent.get("dram_bytes_per_launch")
+    total = 0.0
+    for k in kernels:
+        ent = rec.get(k)
+        if not ent or ent.get("source_hash") != _kernel_source_hash():
+            return None
+        total += float(ent.get("dram_bytes_per_launch"))
+    return total
 
 
 class ClockSampler:
@@ -494,12 +498,13 @@ def run_ours(args):
     list_bytes = 24 * n + 4 * V
     vol_bytes = 24 * n + 4 * words
     roof_list = {"bound": "hbm", "achieved": list_bytes / list_mean / 1e6, "peak": hbm, "unit": "GB/s",
-                 "frac": list_bytes / list_mean / 1e6 / hbm, "traffic": _recorded_traffic("k_generate"),
+                 "frac": list_bytes / list_mean / 1e6 / hbm, "traffic": _recorded_traffic(["k_generate<list32>"]),
                  "kernel": "k_generate<32, list32> (one launch)", "peak_kind": f"{peak_kind} HBM copy",
                  "algorithmic_bytes_per_launch": list_bytes, "ms": list_mean,
                  "bytes_model": "24 B/segment read + 4 B/voxel written"}
     roof_vol = {"bound": "hbm", "achieved": vol_bytes / vol_mean / 1e6, "peak": hbm, "unit": "GB/s",
-                "frac": vol_bytes / vol_mean / 1e6 / hbm, "traffic": _recorded_traffic("k_brick_volume"),
+                "frac": vol_bytes / vol_mean / 1e6 / hbm, "traffic": _recorded_traffic(["k_scan<false>", "k_bin_scatter", "k_brick_volume",
+                                                                  "k_generate<volume, gated>"]),
                 "kernel": ("volume phase: k_generate<volume> (per-voxel atomics)"
                            if tuning and tuning["params"]["volume_path"] == 1 else
                            "volume phase: k_scan<false> + k_bin_scatter + k_brick_volume (one TMA tensor "
