@@ -84,6 +84,27 @@ def _recorded_traffic(kernels):
     return total
 
 
+def _link_bandwidth(dev, h_buf) -> dict:
+    """Host link bandwidth (GB/s) with plain pinned copies of `h_buf`'s size,
+    best of five, each direction."""
+    import torch
+
+    nbytes = h_buf.numel() * h_buf.element_size()
+    d_buf = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    h = h_buf.view(torch.uint8).view(-1)
+    out = {}
+    for name, dst, src in (("d2h", h, d_buf), ("h2d", d_buf, h)):
+        ts = []
+        for _ in range(6):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        out[f"{name}_GBps"] = nbytes / min(ts[1:]) / 1e9
+    return out
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle samples while the timed region runs."""
 
@@ -521,7 +542,9 @@ def run_ours(args):
         h_segs = torch.from_numpy(w.segs).pin_memory()
         h_list = torch.empty(V, dtype=torch.int32).pin_memory()
         h_mask = torch.empty(words, dtype=torch.int32).pin_memory()
-        arena = torch.empty(vox.vox_host_arena_size(n, w.dims, flags, V), dtype=torch.uint8, device=dev)
+        # an arena with room for the brick pieces: the volume by bricks, the list's
+        # copy overlapping the volume's kernels
+        arena = torch.empty(vox.vox_host_arena_size_volume(n, w.dims, flags, V, P), dtype=torch.uint8, device=dev)
         for _ in range(2):
             vox.vox_generate_host(h_segs, w.dims, arena, h_list, h_mask, flags, stream)
         reps = max(3, min(20, args.steps))
@@ -533,10 +556,17 @@ def run_ours(args):
             e2e_t.append(time.perf_counter() - ta)
             assert got == V
         e2e_s = float(np.median(e2e_t))
-        e2e = {"value": total_voxels / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 24 * n,
-               "d2h_bytes_per_step": 4 * V + 4 * words + 8 + 4 + 4, "ms": 1000 * e2e_s,
-               "note": "vox_generate_host: pinned host segments in, list + volume out, median of "
-                       f"{reps} synchronous calls"}
+        h2d_b, d2h_b = 24 * n, 4 * V + 4 * words + 8 + 4 + 4
+        link = _link_bandwidth(dev, h_list)
+        bound_s = h2d_b / (link["h2d_GBps"] * 1e9) + d2h_b / (link["d2h_GBps"] * 1e9)
+        e2e = {"value": total_voxels / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d_b,
+               "d2h_bytes_per_step": d2h_b, "ms": 1000 * e2e_s,
+               "copy_bound": {"h2d_GBps": link["h2d_GBps"], "d2h_GBps": link["d2h_GBps"], "ms": 1000 * bound_s,
+                              "frac": bound_s / e2e_s,
+                              "note": "host link measured here with plain pinned copies; the step cannot beat its "
+                                      "own bytes over it"},
+               "note": "vox_generate_host (brick-sized arena): pinned host segments in, list + fresh "
+                       f"volume out, the list copy overlapping the volume kernels; median of {reps} synchronous calls"}
         del arena
 
     batched = None

@@ -236,11 +236,20 @@ vox_status vox_generate_batched(const vox_segment *d_segs, int64_t n_total, cons
  *   h_mask          host uint32[ceil(w*h*d/32)], OVERWRITTEN with the volume of
  *                   these segments alone (not OR-ed; VOX_OUT_FRESH changes
  *                   nothing here), or NULL
- *   d_arena         device scratch of vox_host_arena_size(...) bytes, 256-byte aligned
+ *   d_arena         device scratch of at least vox_host_arena_size(...) bytes,
+ *                   256-byte aligned. With vox_host_arena_size_volume(...) bytes
+ *                   (room for the brick arrays and piece_capacity pieces, e.g.
+ *                   the count vox_plan returns) the volume is built by bricks and
+ *                   the list's copy to the host overlaps the volume's kernels on
+ *                   a second stream (created once per device by the library);
+ *                   with fewer pieces than needed the volume falls back to
+ *                   atomics on the device, same result.
  *   h_total         receives V (may be NULL)
  *   returns         VOX_OK or the first error, host or device
  */
 size_t vox_host_arena_size(int64_t n, vox_dims dims, int flags, int64_t list_capacity);
+size_t vox_host_arena_size_volume(int64_t n, vox_dims dims, int flags, int64_t list_capacity,
+                                  int64_t piece_capacity);
 vox_status vox_generate_host(const vox_segment *h_segs, int64_t n, vox_dims dims,
                              void *h_list, int64_t list_capacity, uint32_t *h_mask, int flags,
                              void *d_arena, size_t arena_bytes, int64_t *h_total, void *stream);

@@ -536,6 +536,34 @@ vox_status noalloc_scratch(void **out)
     return VOX_OK;
 }
 
+// Bytes of the host-call arena before its workspace: status, segments, list, volume.
+size_t host_arena_prefix(int64_t n, vox_dims dims, int flags, int64_t list_capacity)
+{
+    const size_t elem = (flags & VOX_OUT_LIST64) ? 8 : ((flags & VOX_OUT_LIST32) ? 4 : 0);
+    size_t total = align_up(sizeof(int32_t));                                   // status
+    total += align_up(sizeof(vox_segment) * static_cast<size_t>(n));            // segments
+    total += align_up(elem * static_cast<size_t>(list_capacity));               // list
+    if (flags & VOX_OUT_BITMASK) total += align_up(4 * static_cast<size_t>(vox_mask_words(dims)));
+    return total;
+}
+
+// A second stream per device for the host call's list copy, so that the copy
+// overlaps the volume's kernels. Created on first use, kept for the process.
+cudaStream_t copy_stream()
+{
+    static std::mutex mu;
+    static std::map<int, cudaStream_t> streams;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = streams.find(dev);
+    if (it != streams.end()) return it->second;
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    streams[dev] = s;
+    return s;
+}
+
 }  // namespace
 
 extern "C" {
@@ -717,13 +745,14 @@ vox_status vox_plan(const vox_segment *d_segs, int64_t n, vox_dims dims, void *d
 size_t vox_host_arena_size(int64_t n, vox_dims dims, int flags, int64_t list_capacity)
 {
     if (n < 0 || list_capacity < 0 || check_dims(dims) != VOX_OK) return 0;
-    const size_t elem = (flags & VOX_OUT_LIST64) ? 8 : ((flags & VOX_OUT_LIST32) ? 4 : 0);
-    size_t total = align_up(sizeof(int32_t));                                   // status
-    total += align_up(sizeof(vox_segment) * static_cast<size_t>(n));            // segments
-    total += align_up(elem * static_cast<size_t>(list_capacity));               // list
-    if (flags & VOX_OUT_BITMASK) total += align_up(4 * static_cast<size_t>(vox_mask_words(dims)));
-    total += ws_layout(n).total;                                                // workspace
-    return total;
+    return host_arena_prefix(n, dims, flags, list_capacity) + ws_layout(n).total;
+}
+
+size_t vox_host_arena_size_volume(int64_t n, vox_dims dims, int flags, int64_t list_capacity,
+                                  int64_t piece_capacity)
+{
+    if (n < 0 || list_capacity < 0 || piece_capacity < 0 || check_dims(dims) != VOX_OK) return 0;
+    return host_arena_prefix(n, dims, flags, list_capacity) + vox_workspace_size_volume(n, dims, piece_capacity);
 }
 
 vox_status vox_generate_host(const vox_segment *h_segs, int64_t n, vox_dims dims, void *h_list,
@@ -752,7 +781,9 @@ vox_status vox_generate_host(const vox_segment *h_segs, int64_t n, vox_dims dims
         a += align_up(4 * static_cast<size_t>(words));
     }
     void *d_ws = a;
-    const size_t ws_bytes = ws_layout(n).total;
+    // the workspace takes the rest of the arena: with room for the brick arrays
+    // and pieces (vox_host_arena_size_volume) the volume is built by bricks
+    const size_t ws_bytes = arena_bytes - static_cast<size_t>(a - static_cast<char *>(d_arena));
     if (vox_status e = check_generate_args(n > 0 ? d_segs : nullptr, n, dims, d_list, list_capacity, d_mask, flags,
                                            d_ws, ws_bytes, d_status))
         return e;
@@ -772,15 +803,64 @@ vox_status vox_generate_host(const vox_segment *h_segs, int64_t n, vox_dims dims
     if (h_total) *h_total = V;
     if (st != VOX_OK) return static_cast<vox_status>(st);
     if (has_list && V > list_capacity) return VOX_ERR_CAPACITY;
-    if (bm && cudaMemsetAsync(d_mask, 0, 4 * static_cast<size_t>(words), s) != cudaSuccess) return VOX_ERR_CUDA;
-    if (vox_status e = launch_generate(d_segs, n, dims, d_list, list_capacity, d_mask, flags, d_ws, d_status, s))
-        return e;
-    if (has_list && V > 0 &&
-        cudaMemcpyAsync(h_list, d_list, elem * static_cast<size_t>(V), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return VOX_ERR_CUDA;
-    if (bm && cudaMemcpyAsync(h_mask, d_mask, 4 * static_cast<size_t>(words), cudaMemcpyDeviceToHost, s) !=
-                  cudaSuccess)
-        return VOX_ERR_CUDA;
+    BrickGeom G;
+    const bool bricks = bm && n > 0 && current_tuning().volume_path != VOX_VOLUME_ATOMIC &&
+                        uses_bricks(n, dims, ws_bytes, &G);
+    if (!bricks) {
+        // one pass produces the list and the (cleared) volume together
+        if (bm && cudaMemsetAsync(d_mask, 0, 4 * static_cast<size_t>(words), s) != cudaSuccess) return VOX_ERR_CUDA;
+        if (vox_status e = launch_generate(d_segs, n, dims, d_list, list_capacity, d_mask, flags, d_ws, d_status, s))
+            return e;
+        if (has_list && V > 0 &&
+            cudaMemcpyAsync(h_list, d_list, elem * static_cast<size_t>(V), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return VOX_ERR_CUDA;
+        if (bm && cudaMemcpyAsync(h_mask, d_mask, 4 * static_cast<size_t>(words), cudaMemcpyDeviceToHost, s) !=
+                      cudaSuccess)
+            return VOX_ERR_CUDA;
+    } else {
+        // the list first; its copy to the host runs on a second stream while the
+        // brick-built (fresh) volume is computed, then the volume's copy
+        cudaStream_t s2 = has_list && V > 0 ? copy_stream() : nullptr;
+        if (has_list && V > 0 && s2 == nullptr) return VOX_ERR_CUDA;
+        cudaEvent_t listed = nullptr, copied = nullptr;
+        auto cleanup = [&]() {
+            if (listed) cudaEventDestroy(listed);
+            if (copied) cudaEventDestroy(copied);
+        };
+        const int list_flags = flags & (VOX_OUT_LIST32 | VOX_OUT_LIST64);
+        if (list_flags) {
+            if (vox_status e = launch_generate(d_segs, n, dims, d_list, list_capacity, nullptr, list_flags, d_ws,
+                                               d_status, s))
+                return e;
+        }
+        if (s2 != nullptr) {
+            if (cudaEventCreateWithFlags(&listed, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&copied, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventRecord(listed, s) != cudaSuccess || cudaStreamWaitEvent(s2, listed, 0) != cudaSuccess ||
+                cudaMemcpyAsync(h_list, d_list, elem * static_cast<size_t>(V), cudaMemcpyDeviceToHost, s2) !=
+                    cudaSuccess ||
+                cudaEventRecord(copied, s2) != cudaSuccess) {
+                cleanup();
+                return VOX_ERR_CUDA;
+            }
+        }
+        if (vox_status e = launch_bricks(d_segs, n, G, dims, d_mask, d_ws, ws_bytes, d_status, s, false, true)) {
+            if (copied) cudaStreamWaitEvent(s, copied, 0);
+            cudaStreamSynchronize(s);
+            cleanup();
+            return e;
+        }
+        const bool ok =
+            cudaMemcpyAsync(h_mask, d_mask, 4 * static_cast<size_t>(words), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+            (copied == nullptr || cudaStreamWaitEvent(s, copied, 0) == cudaSuccess);
+        if (!ok) {
+            cudaStreamSynchronize(s);
+            if (s2) cudaStreamSynchronize(s2);
+            cleanup();
+            return VOX_ERR_CUDA;
+        }
+        cleanup();  // destroying a recorded event is allowed; the wait above holds
+    }
     if (cudaMemcpyAsync(&st, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return VOX_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return VOX_ERR_CUDA;
     return static_cast<vox_status>(st);

@@ -39,7 +39,7 @@ EXPORTED = (
     "vox_host_arena_size", "vox_generate_host", "vox_strerror", "vox_mask_words",
     "vox_debug_set_scan_stall", "vox_scan_tile_segments", "vox_generate_noalloc",
     "vox_workspace_size_volume", "vox_plan", "vox_workspace_size_batched", "vox_generate_batched",
-    "vox_set_tuning", "vox_get_tuning",
+    "vox_set_tuning", "vox_get_tuning", "vox_host_arena_size_volume",
 )
 
 VOLUME_AUTO = 0
@@ -93,6 +93,8 @@ def load(path: str | None = None):
         f.restype = i32
     lib.vox_host_arena_size.argtypes = [i64, Dims, i32, i64]
     lib.vox_host_arena_size.restype = sz
+    lib.vox_host_arena_size_volume.argtypes = [i64, Dims, i32, i64, i64]
+    lib.vox_host_arena_size_volume.restype = sz
     lib.vox_generate_host.argtypes = [vp, i64, Dims, vp, i64, vp, i32, vp, sz, vp, vp]
     lib.vox_generate_host.restype = i32
     lib.vox_strerror.argtypes = [i32]
@@ -273,6 +275,11 @@ def vox_generate_noalloc(segs, dims, status, list_out=None, mask=None, flags=Non
 
 def vox_host_arena_size(n: int, dims, flags: int, capacity: int) -> int:
     return int(load().vox_host_arena_size(int(n), _dims(dims), int(flags), int(capacity)))
+
+
+def vox_host_arena_size_volume(n: int, dims, flags: int, capacity: int, piece_capacity: int) -> int:
+    return int(load().vox_host_arena_size_volume(int(n), _dims(dims), int(flags), int(capacity),
+                                                 int(piece_capacity)))
 
 
 def vox_generate_host(h_segs, dims, arena, h_list=None, h_mask=None, flags=None, stream=None):

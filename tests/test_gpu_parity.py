@@ -332,6 +332,42 @@ def test_generate_host_matches():
     assert np.array_equal(h_mask.numpy().view(np.uint32), O.bitmask(w.segs, w.dims))
 
 
+def brick_piece_count(segs, dims):
+    """Pieces of the brick volume, from vox_plan on the device (sizing only)."""
+    d = torch.from_numpy(np.ascontiguousarray(segs)).cuda()
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ws = torch.empty(vox.vox_workspace_size_volume(len(segs), dims, 0), dtype=torch.uint8, device="cuda")
+    return vox.vox_plan(d, dims, ws, st)[1]
+
+
+@pytest.mark.parametrize("which,flags,pieces", [
+    ("config1", L32 | BM, "plan"), ("config1", BM, "plan"), ("config1", L64 | BM, "plan"),
+    ("config1", L32 | BM, 50),       # too few pieces: atomics on the device, same result
+    ("config2", L32 | BM, "plan"),   # the benchmarked e2e call
+])
+def test_generate_host_volume_arena_matches(which, flags, pieces):
+    """The host-buffer call with a brick-sized arena: brick-built volume, list copy
+    overlapped on a second stream; host outputs against the oracle, whole, over
+    stale host buffers."""
+    w = getattr(workloads, which)()
+    O = get_oracle()
+    V = O.total(w.segs)
+    P = brick_piece_count(w.segs, w.dims) if pieces == "plan" else pieces
+    h_segs = torch.from_numpy(w.segs).pin_memory()
+    h_list = None
+    if flags & (L32 | L64):
+        h_list = torch.full((V,), -1, dtype=torch.int64 if flags & L64 else torch.int32).pin_memory()
+    h_mask = torch.full((vox.vox_mask_words(w.dims),), -1, dtype=torch.int32).pin_memory()
+    arena = torch.empty(vox.vox_host_arena_size_volume(w.n, w.dims, flags, V, P), dtype=torch.uint8, device="cuda")
+    for _ in range(2):
+        assert vox.vox_generate_host(h_segs, w.dims, arena, h_list, h_mask, flags) == V
+        if h_list is not None:
+            want = O.list64(w.segs) if flags & L64 else O.list32(w.segs)
+            assert np.array_equal(h_list.numpy().view(want.dtype), want)
+        assert np.array_equal(h_mask.numpy().view(np.uint32), O.bitmask(w.segs, w.dims))
+        h_mask.fill_(-1)
+
+
 def test_repeated_calls_are_stable():
     w = workloads.config2(n_fixed=30000)
     r1 = run_gpu(w.segs, w.dims, L32 | BM)
