@@ -536,6 +536,35 @@ def run_ours(args):
                 "pieces": P}
     roofline, roofline_other = (roof_vol, roof_list) if vol_mean >= list_mean else (roof_list, roof_vol)
 
+    # the brick-major volume layout (VOX_OUT_BRICKED): the same volume phase with one
+    # contiguous bulk copy per brick, and the conversion back to row-major
+    bricked = None
+    if vox.vox_mask_words_bricked(w.dims) > 0:
+        bmask = torch.empty(vox.vox_mask_words_bricked(w.dims), dtype=torch.int32, device=dev)
+        tb, tu = [], []
+        for i in range(min(args.steps, 20) + 3):
+            flush.zero_()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            vox.vox_generate_from_scan(segs, w.dims, ws, status, None, bmask, vox.OUT_BITMASK | vox.OUT_BRICKED,
+                                       stream)
+            e1.record(stream)
+            vox.vox_unbrick(bmask, w.dims, mask, stream)
+            e2.record(stream)
+            torch.cuda.synchronize()
+            if i >= 3:
+                tb.append(e0.elapsed_time(e1))
+                tu.append(e1.elapsed_time(e2))
+        if int(status.item()) != 0:
+            raise RuntimeError(f"device status {vox.strerror(int(status.item()))}")
+        if not torch.equal(mask, graph.mask):
+            raise RuntimeError("unbricked volume differs from the row-major volume")
+        bricked = {"volume_ms": float(np.mean(tb)), "unbrick_ms": float(np.mean(tu)),
+                   "row_major_volume_ms": vol_mean, "brick_shape": vox.vox_brick_shape(w.dims)[0],
+                   "note": "volume phase writing the brick-major layout (one bulk copy per brick) and "
+                           "vox_unbrick back to row-major, checked equal to the row-major volume"}
+        del bmask
+
     # end to end through the host-buffer entry point (copies inside the timed region)
     e2e = None
     if not args.no_e2e:
@@ -604,7 +633,7 @@ def run_ours(args):
         "eager_ms_per_step": float(np.mean(eager_ms)),
         "wall_s_eager_region": wall,
         "roofline": roofline, "roofline_other": roofline_other, "cpu_baseline": cpu, "e2e": e2e,
-        "batched_vs_plain": batched, "serving": served, "sweeps": sweeps,
+        "batched_vs_plain": batched, "serving": served, "sweeps": sweeps, "bricked_volume": bricked,
         "clocks": clocks,
         "gpu_launches": 7 * args.steps,
         "gpu_launches_note": "graph-timed region, per step: k_scan<true>, k_bin_count, k_generate (list), "

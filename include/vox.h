@@ -25,6 +25,19 @@
  *                    (no read of the old volume); the other paths clear the volume
  *                    first. If the call fails on the device (*d_status != 0), the
  *                    volume is either unchanged or cleared.
+ *   VOX_OUT_BRICKED  (with VOX_OUT_BITMASK only) the volume in brick-major layout,
+ *                    written whole like VOX_OUT_FRESH: brick (bx, by, bz) of
+ *                    vox_brick_shape's B0 x B1 x B2 voxels is the `words` =
+ *                    B0*B1*B2/32 words at index (bx + nb0 (by + nb1 bz)) * words,
+ *                    and inside it voxel (lx, ly, lz) is bit lx + B0 (ly + B1 lz)
+ *                    (x fastest; edge bricks padded with zero bits);
+ *                    vox_mask_words_bricked(dims) words, 16-byte aligned. Each
+ *                    brick leaves the GPU as one contiguous bulk copy.
+ *                    vox_unbrick converts to the row-major layout. Needs a width
+ *                    that is a multiple of 32 and a brick workspace
+ *                    (vox_workspace_size_volume; VOX_ERR_WORKSPACE otherwise, and
+ *                    on the device when more pieces than its capacity arise);
+ *                    not accepted by vox_generate_batched / vox_generate_host.
  *   The list holds the voxels of segment 0 (k = 0..N), then segment 1, and so on:
  *   voxel k of segment s sits at index offsets[s] + k, offsets being the exclusive
  *   prefix sum of the per-segment counts N + 1. Voxels shared by two segments
@@ -66,7 +79,8 @@ typedef enum vox_status {
     VOX_ERR_CAPACITY = 4,      /* (device) list capacity below the total voxel count */
     VOX_ERR_TIMEOUT = 5,       /* (device) a bounded wait inside a kernel expired */
     VOX_ERR_CUDA = 6,          /* a CUDA runtime call or launch failed */
-    VOX_ERR_WORKSPACE = 7,     /* workspace NULL, too small or not 256-byte aligned */
+    VOX_ERR_WORKSPACE = 7,     /* workspace NULL, too small or not 256-byte aligned; (device)
+                                  brick-major volume with more pieces than the workspace holds */
     VOX_ERR_ALIGNMENT = 8      /* segments not 16-byte aligned, list/volume misaligned */
 } vox_status;
 
@@ -83,6 +97,7 @@ typedef struct vox_dims {
 #define VOX_OUT_LIST64 2
 #define VOX_OUT_BITMASK 4
 #define VOX_OUT_FRESH 8
+#define VOX_OUT_BRICKED 16
 
 /* Bytes of workspace a call on n segments needs (count, scan and generation of
  * one scene). The workspace is device memory, 256-byte aligned, caller-owned,
@@ -144,6 +159,20 @@ vox_status vox_generate_from_scan(const vox_segment *d_segs, int64_t n, vox_dims
                                   void *d_list, int64_t list_capacity, uint32_t *d_mask,
                                   int flags, void *d_ws, size_t ws_bytes, int32_t *d_status,
                                   void *stream);
+
+/*
+ * Brick-major volumes (VOX_OUT_BRICKED). The brick geometry depends on dims only:
+ * B0 = the largest 32 * 2^k not above min(w, 256), then B1 x B2 power-of-two
+ * rows (B1 = 2 B2 or B2) with B0/32 * B1 * B2 <= 32768 words; w % 32 == 0.
+ *   vox_mask_words_bricked  words of the brick-major volume (0: no geometry)
+ *   vox_brick_shape         h_shape[0..5] = B0, B1, B2, nb0, nb1, nb2 (host
+ *                           int32[6]); VOX_ERR_INVALID_ARG when w % 32 != 0
+ *   vox_unbrick             device brick-major volume -> device row-major volume
+ *                           (vox_mask_words(dims) words), asynchronous on stream
+ */
+int64_t vox_mask_words_bricked(vox_dims dims);
+vox_status vox_brick_shape(vox_dims dims, int32_t *h_shape);
+vox_status vox_unbrick(const uint32_t *d_bricked, vox_dims dims, uint32_t *d_mask, void *stream);
 
 /*
  * The occupancy volume can be built two ways; vox_generate picks one from the

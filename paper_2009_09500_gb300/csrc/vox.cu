@@ -6,6 +6,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstdint>
 #include <cstring>
@@ -120,6 +121,8 @@ vox_status allow_smem(const void *kernel, size_t smem)
     return VOX_OK;
 }
 
+bool make_geom(vox_dims dims, BrickGeom *G);
+
 // Host-side checks shared by the generation entry points.
 vox_status check_generate_args(const vox_segment *segs, int64_t n, vox_dims dims, const void *list,
                                int64_t capacity, const uint32_t *mask, int flags, const void *ws,
@@ -128,10 +131,16 @@ vox_status check_generate_args(const vox_segment *segs, int64_t n, vox_dims dims
     if (n < 0 || status == nullptr) return VOX_ERR_INVALID_ARG;
     if (n > 0 && segs == nullptr) return VOX_ERR_INVALID_ARG;
     if (vox_status e = check_dims(dims)) return e;
-    if (flags & ~(VOX_OUT_LIST32 | VOX_OUT_LIST64 | VOX_OUT_BITMASK | VOX_OUT_FRESH)) return VOX_ERR_INVALID_ARG;
+    if (flags & ~(VOX_OUT_LIST32 | VOX_OUT_LIST64 | VOX_OUT_BITMASK | VOX_OUT_FRESH | VOX_OUT_BRICKED))
+        return VOX_ERR_INVALID_ARG;
     const bool l32 = flags & VOX_OUT_LIST32, l64 = flags & VOX_OUT_LIST64, bm = flags & VOX_OUT_BITMASK;
     if (!(l32 || l64 || bm) || (l32 && l64)) return VOX_ERR_INVALID_ARG;
-    if ((flags & VOX_OUT_FRESH) && !bm) return VOX_ERR_INVALID_ARG;
+    if ((flags & (VOX_OUT_FRESH | VOX_OUT_BRICKED)) && !bm) return VOX_ERR_INVALID_ARG;
+    if (flags & VOX_OUT_BRICKED) {  // the layout exists only with a brick geometry
+        BrickGeom G;
+        if (!make_geom(dims, &G)) return VOX_ERR_INVALID_ARG;
+        if (mask != nullptr && !aligned(mask, 16)) return VOX_ERR_ALIGNMENT;
+    }
     if (l32 && (dims.w > 1024 || dims.h > 1024 || dims.d > 1024)) return VOX_ERR_PACK_WIDTH;
     if ((l32 || l64) && (list == nullptr || capacity < 0)) return VOX_ERR_INVALID_ARG;
     if (bm && mask == nullptr) return VOX_ERR_INVALID_ARG;
@@ -388,7 +397,7 @@ vox_status launch_generate(const vox_segment *segs, int64_t n, vox_dims dims, vo
 // runs if the pieces did not fit in the workspace
 vox_status launch_bricks(const vox_segment *segs, int64_t n, const BrickGeom &G, vox_dims dims, uint32_t *mask,
                          void *ws, size_t ws_bytes, int32_t *status, cudaStream_t stream, bool count_only = false,
-                         bool fresh = false)
+                         bool fresh = false, bool bricked = false)
 {
     // the brick counts come from the count + scan (k_bin_count); the
     // tickets and look-back flags of this pass are reset here, so that the pass
@@ -443,14 +452,16 @@ vox_status launch_bricks(const vox_segment *segs, int64_t n, const BrickGeom &G,
     brp.ticket = reinterpret_cast<uint32_t *>(base + VL.hdr + 128);
     CUtensorMap tmap;
     std::memset(&tmap, 0, sizeof(tmap));
-    brp.use_tma = (mask != nullptr && make_volume_tmap(G, mask, &tmap)) ? 1 : 0;
-    brp.fresh = fresh ? 1 : 0;
+    brp.use_tma = (!bricked && mask != nullptr && make_volume_tmap(G, mask, &tmap)) ? 1 : 0;
+    brp.fresh = (fresh || bricked) ? 1 : 0;
+    brp.bricked = bricked ? 1 : 0;
     const size_t bsmem = sizeof(BrickSmem);
     if (vox_status e = allow_smem(reinterpret_cast<const void *>(k_brick_volume), bsmem)) return e;
     const int bgrid = grid_ctas(reinterpret_cast<const void *>(k_brick_volume), kBrickThreads, bsmem);
     if (bgrid <= 0) return VOX_ERR_CUDA;
     k_brick_volume<<<static_cast<unsigned>(bgrid), kBrickThreads, bsmem, stream>>>(brp, tmap);
     if (cudaGetLastError() != cudaSuccess) return VOX_ERR_CUDA;
+    if (bricked) return VOX_OK;  // no atomics fallback for the brick-major layout (pieces must fit)
     return launch_generate(segs, n, dims, nullptr, 0, mask, VOX_OUT_BITMASK, ws, status, stream,
                            bp.brick_off + G.n_slots, capacity);
 }
@@ -464,6 +475,23 @@ vox_status launch_outputs(const vox_segment *segs, int64_t n, vox_dims dims, voi
     BrickGeom G;
     const bool bm = flags & VOX_OUT_BITMASK;
     const bool fresh = bm && (flags & VOX_OUT_FRESH);
+    const bool bricked = bm && (flags & VOX_OUT_BRICKED);
+    if (bricked) {  // brick-major volume: only the brick path writes it
+        if (!make_geom(dims, &G)) return VOX_ERR_INVALID_ARG;
+        if (n == 0) {
+            if (cudaMemsetAsync(mask, 0, 4 * static_cast<size_t>(G.n_bricks) * static_cast<size_t>(G.words),
+                                stream) != cudaSuccess)
+                return VOX_ERR_CUDA;
+            return VOX_OK;
+        }
+        if (!uses_bricks(n, dims, ws_bytes, &G)) return VOX_ERR_WORKSPACE;
+        const int list_flags = flags & (VOX_OUT_LIST32 | VOX_OUT_LIST64);
+        if (list_flags) {
+            if (vox_status e = launch_generate(segs, n, dims, list, capacity, nullptr, list_flags, ws, status, stream))
+                return e;
+        }
+        return launch_bricks(segs, n, G, dims, mask, ws, ws_bytes, status, stream, false, true, true);
+    }
     const bool bricks =
         n > 0 && bm && current_tuning().volume_path != VOX_VOLUME_ATOMIC && uses_bricks(n, dims, ws_bytes, &G);
     if (!bricks) {
@@ -701,6 +729,37 @@ vox_status vox_generate_batched(const vox_segment *d_segs, int64_t n_total, cons
     return VOX_OK;
 }
 
+int64_t vox_mask_words_bricked(vox_dims dims)
+{
+    BrickGeom G;
+    if (!make_geom(dims, &G)) return 0;
+    return G.n_bricks * static_cast<int64_t>(G.words);
+}
+
+vox_status vox_brick_shape(vox_dims dims, int32_t *h_shape)
+{
+    BrickGeom G;
+    if (h_shape == nullptr || !make_geom(dims, &G)) return VOX_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a) {
+        h_shape[a] = G.B[a];
+        h_shape[3 + a] = G.nb[a];
+    }
+    return VOX_OK;
+}
+
+vox_status vox_unbrick(const uint32_t *d_bricked, vox_dims dims, uint32_t *d_mask, void *stream)
+{
+    BrickGeom G;
+    if (d_bricked == nullptr || d_mask == nullptr || !make_geom(dims, &G)) return VOX_ERR_INVALID_ARG;
+    if (!aligned(d_bricked, 4) || !aligned(d_mask, 4)) return VOX_ERR_ALIGNMENT;
+    const int sms = sm_count();
+    if (sms <= 0) return VOX_ERR_CUDA;
+    const int64_t rows = static_cast<int64_t>(dims.h) * dims.d;
+    const int64_t blocks = std::min<int64_t>((rows + 7) / 8, static_cast<int64_t>(sms) * 16);
+    k_unbrick<<<static_cast<unsigned>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(d_bricked, G, d_mask);
+    return cudaGetLastError() == cudaSuccess ? VOX_OK : VOX_ERR_CUDA;
+}
+
 size_t vox_workspace_size_volume(int64_t n, vox_dims dims, int64_t piece_capacity)
 {
     if (n < 0 || piece_capacity < 0) return 0;
@@ -760,6 +819,7 @@ vox_status vox_generate_host(const vox_segment *h_segs, int64_t n, vox_dims dims
                              int64_t *h_total, void *stream)
 {
     if (n < 0 || (n > 0 && h_segs == nullptr)) return VOX_ERR_INVALID_ARG;
+    if (flags & VOX_OUT_BRICKED) return VOX_ERR_INVALID_ARG;  // host volumes are row-major
     if (vox_status e = check_dims(dims)) return e;
     const bool has_list = flags & (VOX_OUT_LIST32 | VOX_OUT_LIST64);
     const bool bm = flags & VOX_OUT_BITMASK;

@@ -34,6 +34,7 @@ namespace vox {
 constexpr int kBrickThreads = 1024;  // one CTA per SM (the bitmap takes 128 KB)
 constexpr int kBrickWordsMax = 32768;  // 128 KB shared bitmap per brick
 constexpr int32_t kNoStep = 0x7fffffff;
+constexpr int32_t kStPieces = 7;  // VOX_ERR_WORKSPACE: a brick-major volume needs every piece binned
 
 struct BrickGeom {
     int32_t B[3];       // brick extent in voxels per axis (powers of two, B[0] >= 32)
@@ -260,10 +261,11 @@ struct BrickParams {
     const uint64_t *pieces;
     int64_t capacity;
     uint32_t *mask;
-    const int32_t *status;
+    int32_t *status;
     uint32_t *ticket;  // zeroed before launch
     int32_t use_tma;   // merge by one TMA tensor reduce-OR (or store) per brick (tensor map valid)
     int32_t fresh;     // write every brick (zeros included) instead of OR-ing into the volume
+    int32_t bricked;   // brick-major volume: brick b is words `words` at mask + b * words (one bulk copy)
 };
 
 // TMA tensor reduction of a whole brick tile from shared memory into the volume:
@@ -278,6 +280,16 @@ __device__ __forceinline__ void tma_reduce_or_3d(const CUtensorMap *tmap, const 
             reinterpret_cast<uint64_t>(tmap)),
         "r"(x), "r"(y), "r"(z), "r"(smem_addr(smem))
         : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// 1-D bulk copy of a whole brick bitmap to global memory (brick-major volume);
+// both addresses 16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ void bulk_store_1d(void *gmem, const void *smem, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(reinterpret_cast<uint64_t>(gmem)),
+                 "r"(smem_addr(smem)), "r"(bytes)
+                 : "memory");
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
 
@@ -361,7 +373,12 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
     // pieces that did not fit: the gated atomics pass ORs the voxels in (after a
     // fresh volume has been cleared here, brick by brick)
     const bool overflow = __ldg(p.brick_off + p.G.n_slots) > p.capacity;
+    if (overflow && p.bricked) {  // no atomics fallback for this layout
+        if (blockIdx.x == 0 && t == 0) set_status(p.status, kStPieces);
+        return;
+    }
     if (overflow && !p.fresh) return;
+    const bool async_store = p.use_tma || p.bricked;  // the bitmap leaves by the bulk-copy unit
     const BrickGeom &G = p.G;
     const int64_t slots_per_brick = static_cast<int64_t>(kPieceClasses) * G.reps;
     const uint32_t bw = static_cast<uint32_t>(G.B[0]);
@@ -388,7 +405,7 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
             __syncthreads();  // everyone has read the ticket slot before it is rewritten
             continue;
         }
-        if (p.use_tma) {  // the previous brick's reduction must have read the tile
+        if (async_store) {  // the previous brick's copy must have read the tile
             if (t == 0) bulk_wait_read_all();
         }
         __syncthreads();
@@ -435,7 +452,12 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
             __syncwarp();
         }
         __syncthreads();
-        if (p.use_tma) {
+        if (p.bricked) {
+            if (t == 0) {
+                fence_proxy_async_smem();
+                bulk_store_1d(p.mask + b * G.words, sm.bits, static_cast<uint32_t>(G.words) * 4u);
+            }
+        } else if (p.use_tma) {
             if (t == 0) {
                 fence_proxy_async_smem();  // the bitmap's generic writes, visible to the TMA unit
                 if (p.fresh) tma_store_3d(&tmap, sm.bits, X0 / 32, Y0, Z0);
@@ -446,7 +468,28 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
             __syncthreads();
         }
     }
-    if (p.use_tma && t == 0) bulk_wait_all();  // reductions complete before the CTA's memory goes
+    if (async_store && t == 0) bulk_wait_all();  // copies complete before the CTA's memory goes
+}
+
+// Brick-major volume -> row-major volume: one warp per volume row (y, z), lanes
+// over the row's words; each word comes from its brick's row (bxw contiguous
+// words), so reads stay sector-sized and writes are coalesced.
+__global__ void __launch_bounds__(256) k_unbrick(const uint32_t *bricked, BrickGeom G, uint32_t *mask)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t rows = static_cast<int64_t>(G.dim[1]) * G.dim[2];
+    const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x / 32);
+    for (int64_t r = static_cast<int64_t>(blockIdx.x) * (blockDim.x / 32) + (threadIdx.x >> 5); r < rows; r += warps) {
+        const int32_t y = static_cast<int32_t>(r % G.dim[1]);
+        const int32_t z = static_cast<int32_t>(r / G.dim[1]);
+        const int64_t bbase = static_cast<int64_t>(G.nb[0]) * ((y >> G.logB[1]) + static_cast<int64_t>(G.nb[1]) * (z >> G.logB[2]));
+        const int64_t inrow = static_cast<int64_t>(G.bxw) * ((y & (G.B[1] - 1)) + static_cast<int64_t>(G.B[1]) * (z & (G.B[2] - 1)));
+        uint32_t *out = mask + r * G.row_words;
+        for (int32_t xw = lane; xw < G.row_words; xw += 32) {
+            const int64_t brick = bbase + (xw >> G.log_bxw);
+            out[xw] = __ldg(bricked + brick * G.words + inrow + (xw & (G.bxw - 1)));
+        }
+    }
 }
 
 }  // namespace vox

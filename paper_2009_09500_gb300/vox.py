@@ -33,6 +33,7 @@ OUT_LIST32 = 1
 OUT_LIST64 = 2
 OUT_BITMASK = 4
 OUT_FRESH = 8
+OUT_BRICKED = 16
 
 EXPORTED = (
     "vox_workspace_size", "vox_count", "vox_generate", "vox_generate_from_scan",
@@ -40,6 +41,7 @@ EXPORTED = (
     "vox_debug_set_scan_stall", "vox_scan_tile_segments", "vox_generate_noalloc",
     "vox_workspace_size_volume", "vox_plan", "vox_workspace_size_batched", "vox_generate_batched",
     "vox_set_tuning", "vox_get_tuning", "vox_host_arena_size_volume",
+    "vox_mask_words_bricked", "vox_brick_shape", "vox_unbrick",
 )
 
 VOLUME_AUTO = 0
@@ -95,6 +97,12 @@ def load(path: str | None = None):
     lib.vox_host_arena_size.restype = sz
     lib.vox_host_arena_size_volume.argtypes = [i64, Dims, i32, i64, i64]
     lib.vox_host_arena_size_volume.restype = sz
+    lib.vox_mask_words_bricked.argtypes = [Dims]
+    lib.vox_mask_words_bricked.restype = i64
+    lib.vox_brick_shape.argtypes = [Dims, vp]
+    lib.vox_brick_shape.restype = i32
+    lib.vox_unbrick.argtypes = [vp, Dims, vp, vp]
+    lib.vox_unbrick.restype = i32
     lib.vox_generate_host.argtypes = [vp, i64, Dims, vp, i64, vp, i32, vp, sz, vp, vp]
     lib.vox_generate_host.restype = i32
     lib.vox_strerror.argtypes = [i32]
@@ -275,6 +283,26 @@ def vox_generate_noalloc(segs, dims, status, list_out=None, mask=None, flags=Non
 
 def vox_host_arena_size(n: int, dims, flags: int, capacity: int) -> int:
     return int(load().vox_host_arena_size(int(n), _dims(dims), int(flags), int(capacity)))
+
+
+def vox_mask_words_bricked(dims) -> int:
+    return int(load().vox_mask_words_bricked(_dims(dims)))
+
+
+def vox_brick_shape(dims):
+    """((B0, B1, B2), (nb0, nb1, nb2)) of the brick-major layout for dims."""
+    out = (ctypes.c_int32 * 6)()
+    st = load().vox_brick_shape(_dims(dims), out)
+    if st != OK:
+        raise VoxError(st, "vox_brick_shape")
+    return tuple(out[:3]), tuple(out[3:])
+
+
+def vox_unbrick(bricked, dims, mask, stream=None):
+    """Brick-major volume (device int32 tensor) -> row-major volume `mask`."""
+    st = load().vox_unbrick(_ptr(bricked), _dims(dims), _ptr(mask), _stream(stream))
+    if st != OK:
+        raise VoxError(st, "vox_unbrick")
 
 
 def vox_host_arena_size_volume(n: int, dims, flags: int, capacity: int, piece_capacity: int) -> int:

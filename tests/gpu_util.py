@@ -14,7 +14,8 @@ SENTINEL32 = -0x21524111  # 0xDEADBEEF as int32
 SENTINEL64 = -0x2152411021524111
 
 
-def run_gpu(segs_np, dims, flags, capacity=None, extra=64, mask_init=None, use_from_scan=False, pieces=None):
+def run_gpu(segs_np, dims, flags, capacity=None, extra=64, mask_init=None, use_from_scan=False, pieces=None,
+            mask_words=None):
     """vox_count then vox_generate (or vox_generate_from_scan) on cuda:0.
     The list gets ``extra`` sentinel elements past the capacity the call is told
     about, to catch writes beyond it. ``pieces``: None for the plain workspace
@@ -49,7 +50,7 @@ def run_gpu(segs_np, dims, flags, capacity=None, extra=64, mask_init=None, use_f
         list_t = torch.full((capacity + extra,), SENTINEL32, dtype=torch.int32, device="cuda")
     mask_t = None
     if flags & vox.OUT_BITMASK:
-        words = vox.vox_mask_words(dims)
+        words = vox.vox_mask_words(dims) if mask_words is None else mask_words
         if mask_init is None:
             mask_t = torch.zeros(words, dtype=torch.int32, device="cuda")
         else:
@@ -135,3 +136,16 @@ def brick_pieces_expected(O, segs, dims):
     bc = xyz // B
     change = np.any(bc[1:] != bc[:-1], axis=1) & ~starts[1:]
     return int(starts.sum() + change.sum())
+
+
+def bricked_from_row_major(mask_u32: np.ndarray, dims) -> np.ndarray:
+    """The brick-major layout of a row-major volume, rearranged with numpy from
+    the layout documented for VOX_OUT_BRICKED (brick (bx, by, bz) at index
+    bx + nb0 (by + nb1 bz), x fastest inside a brick, edge bricks zero-padded)."""
+    (b0, b1, b2), (n0, n1, n2) = vox.vox_brick_shape(dims)
+    w, h, d = (int(v) for v in dims)
+    bits = np.unpackbits(mask_u32.view(np.uint8), bitorder="little")[: w * h * d].reshape(d, h, w)
+    pad = np.zeros((n2 * b2, n1 * b1, n0 * b0), dtype=np.uint8)
+    pad[:d, :h, :w] = bits
+    bricks = pad.reshape(n2, b2, n1, b1, n0, b0).transpose(0, 2, 4, 1, 3, 5)
+    return np.packbits(np.ascontiguousarray(bricks).reshape(-1), bitorder="little").view(np.uint32)

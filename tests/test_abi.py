@@ -70,3 +70,15 @@ def test_binding_has_no_oracle_import():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "liboracle" not in text, f
+
+
+def test_brick_shape_queries(lib):
+    """The brick geometry follows the documented rule (host-only queries)."""
+    assert vox.vox_brick_shape((1024, 1024, 1024)) == ((256, 64, 64), (4, 16, 16))
+    assert vox.vox_mask_words_bricked((1024, 1024, 1024)) == (1 << 30) // 32
+    assert vox.vox_brick_shape((96, 40, 17)) == ((64, 128, 128), (2, 1, 1))
+    assert vox.vox_mask_words_bricked((96, 40, 17)) == 2 * 64 * 128 * 128 // 32
+    assert vox.vox_brick_shape((32, 7, 5)) == ((32, 256, 128), (1, 1, 1))
+    assert vox.vox_mask_words_bricked((13, 7, 5)) == 0
+    with pytest.raises(vox.VoxError):
+        vox.vox_brick_shape((13, 7, 5))

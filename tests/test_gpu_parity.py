@@ -10,8 +10,8 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_util import (assert_list_equal, brick_pieces_expected, check_mask_sparse, get_oracle, oracle_list,
-                      run_gpu, sparse_mask_from_list64)
+from gpu_util import (assert_list_equal, brick_pieces_expected, bricked_from_row_major, check_mask_sparse,
+                      get_oracle, oracle_list, run_gpu, sparse_mask_from_list64)
 from paper_2009_09500_gb300 import vox, workloads
 
 pytestmark = pytest.mark.gpu
@@ -562,3 +562,73 @@ def test_fresh_without_bitmask_is_rejected():
     with pytest.raises(vox.VoxError) as e:
         vox.vox_generate(segs, (8, 8, 8), ws, st, lst, flags=L32 | FR)
     assert e.value.status == vox.ERR_INVALID_ARG
+
+
+# --------------------------------------------- brick-major volumes (VOX_OUT_BRICKED)
+BR = vox.OUT_BRICKED
+
+
+@pytest.mark.parametrize("dims,flags", [
+    ((256, 256, 256), BM | BR),
+    ((256, 256, 256), L32 | BM | BR),
+    ((96, 40, 17), BM | BR),       # one padded brick of 64 x 128 x 128
+    ((32, 7, 5), BM | BR),
+    ((128, 128, 64), L64 | BM | BR),
+])
+def test_bricked_volume_matches_layout(dims, flags):
+    """Brick-major volume against the oracle's volume rearranged by the
+    documented layout, over a buffer of stale bits; vox_unbrick back to the
+    oracle's row-major volume."""
+    rng = np.random.default_rng(sum(dims) + flags)
+    segs = workloads.uniform_segments(rng, 3000, dims)
+    O = get_oracle()
+    words = vox.vox_mask_words_bricked(dims)
+    init = rng.integers(0, 2**32, size=words, dtype=np.uint64).astype(np.uint32)
+    r = run_gpu(segs, dims, flags, pieces="plan", mask_words=words, mask_init=init)
+    assert r["status"] == 0
+    want_rm = O.bitmask(segs, dims)
+    assert np.array_equal(r["mask"], bricked_from_row_major(want_rm, dims))
+    if flags & (L32 | L64):
+        assert_list_equal(r["list_full"], oracle_list(O, segs, flags), r["V"])
+    bricked = torch.from_numpy(r["mask"].view(np.int32).copy()).cuda()
+    row = torch.full((vox.vox_mask_words(dims),), -1, dtype=torch.int32, device="cuda")
+    vox.vox_unbrick(bricked, dims, row)
+    torch.cuda.synchronize()
+    assert np.array_equal(row.cpu().numpy().view(np.uint32), want_rm)
+
+
+def test_bricked_config2_full_size():
+    w = workloads.config2()
+    O = get_oracle()
+    words = vox.vox_mask_words_bricked(w.dims)
+    assert words == vox.vox_mask_words(w.dims)  # 1024^3: bricks tile the volume exactly
+    r = run_gpu(w.segs, w.dims, L32 | BM | BR, pieces="plan", mask_words=words, use_from_scan=True)
+    assert r["status"] == 0
+    assert np.array_equal(r["mask"], bricked_from_row_major(O.bitmask(w.segs, w.dims), w.dims))
+
+
+def test_bricked_errors_and_empty():
+    rng = np.random.default_rng(81)
+    dims = (256, 64, 64)
+    segs = workloads.uniform_segments(rng, 500, dims)
+    words = vox.vox_mask_words_bricked(dims)
+    # plain workspace (no brick arrays): refused on the host, nothing launched
+    with pytest.raises(vox.VoxError) as e:
+        run_gpu(segs, dims, BM | BR, mask_words=words)
+    assert e.value.status == vox.ERR_WORKSPACE
+    # pieces beyond the workspace's capacity: reported on the device
+    r = run_gpu(segs, dims, BM | BR, pieces=10, mask_words=words)
+    assert r["status"] == vox.ERR_WORKSPACE
+    # the layout needs w % 32 == 0; bricked needs the volume flag
+    assert vox.vox_mask_words_bricked((13, 7, 5)) == 0
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    d = torch.from_numpy(segs).cuda()
+    ws = torch.empty(vox.vox_workspace_size_volume(500, dims, 4000), dtype=torch.uint8, device="cuda")
+    lst = torch.empty(100000, dtype=torch.int32, device="cuda")
+    with pytest.raises(vox.VoxError) as e:
+        vox.vox_generate(d, dims, ws, st, lst, None, flags=L32 | BR)
+    assert e.value.status == vox.ERR_INVALID_ARG
+    # no segments: the whole brick-major buffer is cleared
+    r = run_gpu(np.zeros((0, 6), np.int32), dims, BM | BR, mask_words=words,
+                mask_init=np.full(words, 0xFFFFFFFF, np.uint32), pieces=1)
+    assert r["status"] == 0 and (r["mask"] == 0).all()
