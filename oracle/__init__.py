@@ -72,6 +72,19 @@ def load(path: str | None = None):
     lib.oracle_sectors_touched.restype = i64
     lib.oracle_popcount.argtypes = [p, i64]
     lib.oracle_popcount.restype = i64
+    lib.oracle_isqrt.argtypes = [i64]
+    lib.oracle_isqrt.restype = i64
+    lib.oracle_euclid_steps.argtypes = [p]
+    lib.oracle_euclid_steps.restype = i64
+    lib.oracle_euclid_voxel.argtypes = [p, i64, p]
+    lib.oracle_euclid_voxel.restype = None
+    lib.oracle_euclid_count.argtypes = [p, i64, p]
+    lib.oracle_euclid_count.restype = i64
+    for name in ("oracle_euclid_list32", "oracle_euclid_list64"):
+        getattr(lib, name).argtypes = [p, i64, p, i64]
+        getattr(lib, name).restype = i64
+    lib.oracle_euclid_bitmask.argtypes = [p, i64, p, p, i64]
+    lib.oracle_euclid_bitmask.restype = i64
     if path == _LIB:
         _lib = lib
     return lib
@@ -173,6 +186,49 @@ class Oracle:
     def popcount(self, mask: np.ndarray) -> int:
         m = np.ascontiguousarray(mask, dtype=np.uint32)
         return int(self.lib.oracle_popcount(self._ptr(m), m.shape[0]))
+
+    # ---- the Euclidean-N variant (Eq. (1)-(2) read literally, repeats removed)
+    def isqrt(self, x: int) -> int:
+        return int(self.lib.oracle_isqrt(int(x)))
+
+    def euclid_steps(self, seg) -> int:
+        a = self._segs(np.asarray(seg).reshape(1, 6))
+        return int(self.lib.oracle_euclid_steps(self._ptr(a)))
+
+    def euclid_voxel(self, seg, k: int):
+        a = self._segs(np.asarray(seg).reshape(1, 6))
+        out = np.zeros(3, dtype=np.int64)
+        self.lib.oracle_euclid_voxel(self._ptr(a), int(k), self._ptr(out))
+        return tuple(int(v) for v in out)
+
+    def euclid_count(self, segs) -> np.ndarray:
+        a = self._segs(segs)
+        out = np.zeros(a.shape[0], dtype=np.int64)
+        self.lib.oracle_euclid_count(self._ptr(a), a.shape[0], self._ptr(out))
+        return out
+
+    def euclid_list32(self, segs) -> np.ndarray:
+        a = self._segs(segs)
+        v = int(self.lib.oracle_euclid_count(self._ptr(a), a.shape[0], None))
+        out = np.zeros(v, dtype=np.uint32)
+        assert self.lib.oracle_euclid_list32(self._ptr(a), a.shape[0], self._ptr(out), v) == v
+        return out
+
+    def euclid_list64(self, segs) -> np.ndarray:
+        a = self._segs(segs)
+        v = int(self.lib.oracle_euclid_count(self._ptr(a), a.shape[0], None))
+        out = np.zeros(v, dtype=np.uint64)
+        assert self.lib.oracle_euclid_list64(self._ptr(a), a.shape[0], self._ptr(out), v) == v
+        return out
+
+    def euclid_bitmask(self, segs, dims, mask: np.ndarray | None = None) -> np.ndarray:
+        a = self._segs(segs)
+        d = np.ascontiguousarray(dims, dtype=np.int32)
+        if mask is None:
+            mask = np.zeros(self.mask_words(dims), dtype=np.uint32)
+        got = self.lib.oracle_euclid_bitmask(self._ptr(a), a.shape[0], self._ptr(d), self._ptr(mask), mask.shape[0])
+        assert got >= 0, "a voxel fell outside the volume"
+        return mask
 
 
 _default = None

@@ -62,10 +62,9 @@ static int64_t nearest_away_from_start(int64_t s, __int128 num, int64_t den)
     return num < 0 ? s - (int64_t)q : s + (int64_t)q;
 }
 
-/* Voxel k of a segment: the lattice point nearest to G_k = S + W*k (Eq. (3)). */
-void oracle_voxel(const int32_t *seg, int64_t k, int64_t *out3)
+/* Sample k with N steps: the lattice point nearest to G_k = S + W*k, W = (E-S)/N. */
+static void voxel_of_sample(const int32_t *seg, int64_t k, int64_t N, int64_t *out3)
 {
-    int64_t N = oracle_steps(seg);
     for (int a = 0; a < 3; ++a) {
         int64_t S = seg[a];
         int64_t E = seg[3 + a];
@@ -77,6 +76,12 @@ void oracle_voxel(const int32_t *seg, int64_t k, int64_t *out3)
             out3[a] = nearest_away_from_start(S, num, N);
         }
     }
+}
+
+/* Voxel k of a segment: the lattice point nearest to G_k = S + W*k (Eq. (3)). */
+void oracle_voxel(const int32_t *seg, int64_t k, int64_t *out3)
+{
+    voxel_of_sample(seg, k, oracle_steps(seg), out3);
 }
 
 /* Validation of a call: dims in [1, 2^21]; every endpoint inside [0, dim);
@@ -114,6 +119,17 @@ void oracle_offsets(const int32_t *counts, int64_t n, int64_t *offsets)
     offsets[n] = run;
 }
 
+/* The packed list encodings of one voxel. */
+static uint32_t pack32(const int64_t *v)
+{
+    return (uint32_t)v[0] | ((uint32_t)v[1] << 10) | ((uint32_t)v[2] << 20);
+}
+
+static uint64_t pack64(const int64_t *v)
+{
+    return (uint64_t)v[0] | ((uint64_t)v[1] << 21) | ((uint64_t)v[2] << 42);
+}
+
 /* Fig. 3 for every segment in order: append voxel k for k = 0..N.
  * At most `cap` words are written; the return value is V, the number the
  * segments produce, so V > cap tells the caller the buffer was too small. */
@@ -126,8 +142,7 @@ int64_t oracle_list32(const int32_t *segs, int64_t n, uint32_t *out, int64_t cap
         for (int64_t k = 0; k <= N; ++k) {
             int64_t v[3];
             oracle_voxel(seg, k, v);
-            if (g < cap)
-                out[g] = (uint32_t)v[0] | ((uint32_t)v[1] << 10) | ((uint32_t)v[2] << 20);
+            if (g < cap) out[g] = pack32(v);
             ++g;
         }
     }
@@ -143,12 +158,17 @@ int64_t oracle_list64(const int32_t *segs, int64_t n, uint64_t *out, int64_t cap
         for (int64_t k = 0; k <= N; ++k) {
             int64_t v[3];
             oracle_voxel(seg, k, v);
-            if (g < cap)
-                out[g] = (uint64_t)v[0] | ((uint64_t)v[1] << 21) | ((uint64_t)v[2] << 42);
+            if (g < cap) out[g] = pack64(v);
             ++g;
         }
     }
     return g;
+}
+
+/* Sets bit lin of the volume: bit lin % 32 of word lin / 32 (little-endian). */
+static void set_bit(uint32_t *mask, uint64_t lin)
+{
+    mask[lin / 32] |= (uint32_t)1 << (lin % 32);
 }
 
 /* OR every voxel of every segment into the occupancy volume of n_words words.
@@ -167,7 +187,7 @@ int64_t oracle_bitmask(const int32_t *segs, int64_t n, const int32_t *dims, uint
             oracle_voxel(seg, k, v);
             uint64_t lin = (uint64_t)(v[0] + w * (v[1] + h * v[2]));
             if (lin / 32 < (uint64_t)n_words)
-                mask[lin / 32] |= (uint32_t)1 << (lin % 32);
+                set_bit(mask, lin);
             else
                 outside = 1;
             ++g;
@@ -217,4 +237,141 @@ int64_t oracle_popcount(const uint32_t *mask, int64_t n_words)
         while (x) { x &= x - 1; ++c; }
     }
     return c;
+}
+
+/*
+ * The Euclidean-N variant: Eq. (1)-(2) read literally. N = int(|E - S|), the
+ * integer part of the Euclidean length, i.e. the largest integer whose square
+ * does not exceed dx^2 + dy^2 + dz^2. The samples are again G_k = S + W k,
+ * W = (E - S) / N, k = 0..N, each mapped to its nearest lattice point (ties
+ * away from S); since N can exceed the largest |d_a|, two samples can fall in
+ * one voxel, and the voxel set V of Fig. 3 holds it once. The samples move
+ * monotonically along each axis, by at most one voxel per step, so a repeated
+ * voxel is always the previous sample's: a voxel is added when it differs from
+ * the previous sample's voxel. N = 0 (S == E) gives the single voxel S.
+ */
+
+/* Integer square root, digit by digit in base 4: the largest r with r*r <= x. */
+int64_t oracle_isqrt(int64_t x)
+{
+    uint64_t v = (uint64_t)x, r = 0, bit = (uint64_t)1 << 62;
+    while (bit > v) bit >>= 2;
+    while (bit) {
+        if (v >= r + bit) {
+            v -= r + bit;
+            r = (r >> 1) + bit;
+        } else {
+            r >>= 1;
+        }
+        bit >>= 2;
+    }
+    return (int64_t)r;
+}
+
+/* N of Eq. (1): int(|E - S|). */
+int64_t oracle_euclid_steps(const int32_t *seg)
+{
+    int64_t sq = 0;
+    for (int a = 0; a < 3; ++a) {
+        int64_t d = (int64_t)seg[3 + a] - (int64_t)seg[a];
+        sq += d * d;
+    }
+    return oracle_isqrt(sq);
+}
+
+/* The voxel of sample k with the Euclidean N. */
+void oracle_euclid_voxel(const int32_t *seg, int64_t k, int64_t *out3)
+{
+    voxel_of_sample(seg, k, oracle_euclid_steps(seg), out3);
+}
+
+/* Walks the samples of one segment and calls back for every voxel added. */
+typedef void (*oracle_emit_fn)(void *ctx, const int64_t *v);
+
+static int64_t euclid_segment(const int32_t *seg, oracle_emit_fn emit, void *ctx)
+{
+    int64_t N = oracle_euclid_steps(seg);
+    int64_t prev[3] = {0, 0, 0};
+    int64_t added = 0;
+    for (int64_t k = 0; k <= N; ++k) {
+        int64_t v[3];
+        oracle_euclid_voxel(seg, k, v);
+        if (k > 0 && v[0] == prev[0] && v[1] == prev[1] && v[2] == prev[2]) continue;
+        if (emit) emit(ctx, v);
+        prev[0] = v[0];
+        prev[1] = v[1];
+        prev[2] = v[2];
+        ++added;
+    }
+    return added;
+}
+
+/* Voxels per segment (int64) and their total. */
+int64_t oracle_euclid_count(const int32_t *segs, int64_t n, int64_t *counts)
+{
+    int64_t total = 0;
+    for (int64_t s = 0; s < n; ++s) {
+        int64_t c = euclid_segment(segs + 6 * s, 0, 0);
+        if (counts) counts[s] = c;
+        total += c;
+    }
+    return total;
+}
+
+struct list_ctx {
+    void *out;
+    int64_t cap, g;
+    int wide;
+};
+
+static void emit_list(void *p, const int64_t *v)
+{
+    struct list_ctx *c = (struct list_ctx *)p;
+    if (c->g < c->cap) {
+        if (c->wide)
+            ((uint64_t *)c->out)[c->g] = pack64(v);
+        else
+            ((uint32_t *)c->out)[c->g] = pack32(v);
+    }
+    ++c->g;
+}
+
+int64_t oracle_euclid_list32(const int32_t *segs, int64_t n, uint32_t *out, int64_t cap)
+{
+    struct list_ctx c = {out, cap, 0, 0};
+    for (int64_t s = 0; s < n; ++s) euclid_segment(segs + 6 * s, emit_list, &c);
+    return c.g;
+}
+
+int64_t oracle_euclid_list64(const int32_t *segs, int64_t n, uint64_t *out, int64_t cap)
+{
+    struct list_ctx c = {out, cap, 0, 1};
+    for (int64_t s = 0; s < n; ++s) euclid_segment(segs + 6 * s, emit_list, &c);
+    return c.g;
+}
+
+struct mask_ctx {
+    uint32_t *mask;
+    int64_t w, h, n_words;
+    int outside;
+};
+
+static void emit_mask(void *p, const int64_t *v)
+{
+    struct mask_ctx *c = (struct mask_ctx *)p;
+    uint64_t lin = (uint64_t)(v[0] + c->w * (v[1] + c->h * v[2]));
+    if (lin / 32 < (uint64_t)c->n_words)
+        set_bit(c->mask, lin);
+    else
+        c->outside = 1;
+}
+
+/* OR the variant's voxels into the volume; -1 if a voxel fell outside it. */
+int64_t oracle_euclid_bitmask(const int32_t *segs, int64_t n, const int32_t *dims, uint32_t *mask,
+                              int64_t n_words)
+{
+    struct mask_ctx c = {mask, dims[0], dims[1], n_words, 0};
+    int64_t g = 0;
+    for (int64_t s = 0; s < n; ++s) g += euclid_segment(segs + 6 * s, emit_mask, &c);
+    return c.outside ? -1 : g;
 }

@@ -23,6 +23,7 @@ as close as possible to the segment):
 from __future__ import annotations
 
 import itertools
+import math
 import os
 from fractions import Fraction
 
@@ -337,3 +338,139 @@ def pin_validate(O):
 
 
 ALL_FAST_PINS = (pin_hand_voxels, pin_hand_packing, pin_closed_forms, pin_scan, pin_validate)
+
+
+# ------------------------------------------- the Euclidean-N variant (Eq. (1)-(2))
+def parse_hand_euclid():
+    cases = []
+    with open(os.path.join(GOLDEN, "hand_euclid.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            seg_s, vox_s = line.split(":")
+            cases.append(([int(v) for v in seg_s.split()], [tuple(int(v) for v in t.split()) for t in vox_s.split(";")]))
+    return cases
+
+
+def unpack64(l64):
+    m = np.uint64((1 << 21) - 1)
+    return np.stack([(l64 & m), (l64 >> np.uint64(21)) & m, (l64 >> np.uint64(42)) & m], 1).astype(np.int64)
+
+
+def euclid_xyz(O, seg):
+    return [tuple(r) for r in unpack64(O.euclid_list64(np.array([seg], dtype=np.int32))).tolist()]
+
+
+def pin_euclid_hand(O):
+    for seg, vox in parse_hand_euclid():
+        assert euclid_xyz(O, seg) == vox, (seg, euclid_xyz(O, seg), vox)
+        assert int(O.euclid_count(np.array([seg], dtype=np.int32))[0]) == len(vox)
+
+
+def pin_euclid_isqrt(O):
+    """N = int(|d|) against Python's integer square root, on squares, their
+    neighbours and random values up to 3 (2^21 - 1)^2."""
+    rng = np.random.default_rng(5)
+    top = 3 * ((1 << 21) - 1) ** 2
+    xs = [0, 1, 2, 3, 4, 5, 8, 9, 10, 15, 16, 17, top]
+    for r in [2, 3, 46340, 46341, 1 << 20, (1 << 21) - 1, 3631212]:
+        xs += [r * r - 1, r * r, r * r + 1]
+    xs += [int(v) for v in rng.integers(0, top, size=2000)]
+    for x in xs:
+        assert O.isqrt(x) == math.isqrt(x), x
+    for seg in rng.integers(0, 1 << 21, size=(200, 6)).tolist():
+        d2 = sum((seg[3 + a] - seg[a]) ** 2 for a in range(3))
+        assert O.euclid_steps(seg) == math.isqrt(d2)
+
+
+def euclid_brute_force(seg):
+    """Independent of any rounding formula: N = the largest integer with N^2 <=
+    |d|^2 (by search); per sample k and axis, every coordinate between S and E is
+    scored by |N (v - S) - k d| (the distance to G_k scaled by N), the smallest
+    wins, a tie goes to the coordinate farther from S; repeats of the previous
+    voxel are dropped."""
+    S = [int(v) for v in seg[:3]]
+    E = [int(v) for v in seg[3:]]
+    d = [E[a] - S[a] for a in range(3)]
+    d2 = sum(x * x for x in d)
+    N = 0
+    while (N + 1) * (N + 1) <= d2:
+        N += 1
+    if N == 0:
+        return [tuple(S)]
+    out = []
+    for k in range(N + 1):
+        v = []
+        for a in range(3):
+            lo, hi = min(S[a], E[a]), max(S[a], E[a])
+            best = None
+            for c in range(lo, hi + 1):
+                key = (abs(N * (c - S[a]) - k * d[a]), -abs(c - S[a]))
+                if best is None or key < best[0]:
+                    best = (key, c)
+            v.append(best[1])
+        if not out or tuple(v) != out[-1]:
+            out.append(tuple(v))
+    return out
+
+
+def pin_euclid_brute_force(O, segs):
+    segs = np.asarray(segs, dtype=np.int32)
+    counts = O.euclid_count(segs)
+    xyz = unpack64(O.euclid_list64(segs))
+    off = np.concatenate([[0], np.cumsum(counts)])
+    for s in range(len(segs)):
+        want = euclid_brute_force(segs[s].tolist())
+        got = [tuple(r) for r in xyz[off[s]:off[s + 1]].tolist()]
+        assert got == want, (segs[s].tolist(), got, want)
+
+
+def pin_euclid_closed_forms(O):
+    """Where |d| = max|d_a| (one non-zero axis) or all non-zero axes move together
+    (pure diagonals), the variant's voxels are those of N = max|d|."""
+    rng = np.random.default_rng(6)
+    segs = []
+    for _ in range(300):
+        t = int(rng.integers(0, 2000))
+        s = rng.integers(0, 4000, size=3)
+        sign = rng.choice([-1, 1], size=3)
+        for mask in ([1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 0], [0, 1, 1], [1, 0, 1], [1, 1, 1]):
+            e = s + sign * t * np.array(mask)
+            segs.append(np.concatenate([s, e]) + 2000)
+    segs = np.array(segs, dtype=np.int32)
+    assert np.array_equal(O.euclid_list64(segs), O.list64(segs))
+
+
+def pin_euclid_invariants(O, segs):
+    """Per segment: first voxel S, last E; between N_max + 1 and N + 1 voxels
+    (N_max = max|d_a|, N = int(|d|)); every step moves each axis by 0 or one voxel
+    toward E and at least one axis; no voxel twice."""
+    segs = np.asarray(segs, dtype=np.int32)
+    counts = O.euclid_count(segs)
+    xyz = unpack64(O.euclid_list64(segs))
+    off = np.concatenate([[0], np.cumsum(counts)])
+    assert off[-1] == len(xyz)
+    for s in range(len(segs)):
+        S, E = segs[s, :3].astype(np.int64), segs[s, 3:].astype(np.int64)
+        v = xyz[off[s]:off[s + 1]]
+        nmax = int(np.abs(E - S).max())
+        ne = math.isqrt(int(((E - S) ** 2).sum()))
+        assert nmax + 1 <= len(v) <= ne + 1, (segs[s], len(v), nmax, ne)
+        assert tuple(v[0]) == tuple(S) and tuple(v[-1]) == tuple(E)
+        if len(v) > 1:
+            step = np.diff(v, axis=0)
+            assert (np.abs(step) <= 1).all() and (np.abs(step).sum(1) >= 1).all()
+            assert ((step * np.sign(E - S)) >= 0).all()
+        assert len(np.unique(v, axis=0)) == len(v)
+
+
+def pin_euclid_volume(O, segs, dims):
+    """The variant's volume holds exactly the distinct voxels of its list."""
+    segs = np.asarray(segs, dtype=np.int32)
+    xyz = unpack64(O.euclid_list64(segs))
+    w, h, _ = dims
+    lin = np.unique(xyz[:, 0] + w * (xyz[:, 1] + h * xyz[:, 2]))
+    want = np.zeros(O.mask_words(dims), dtype=np.uint32)
+    np.bitwise_or.at(want, lin // 32, (np.uint64(1) << (lin % 32).astype(np.uint64)).astype(np.uint32))
+    assert np.array_equal(O.euclid_bitmask(segs, dims), want)

@@ -136,3 +136,37 @@ def test_euclidean_length_gives_repeats():
     for k in range(n_euc + 1):
         pts.append(tuple(P._nearest_from_fraction(S[a], Fraction((E[a] - S[a]) * k, n_euc), 1) for a in range(3)))
     assert len(set(pts)) < len(pts)
+
+
+# ---------------------------------------------- the Euclidean-N variant (Eq. (1)-(2))
+def test_euclid_hand(orc):
+    P.pin_euclid_hand(orc)
+
+
+def test_euclid_isqrt(orc):
+    P.pin_euclid_isqrt(orc)
+
+
+def test_euclid_brute_force_all_pairs_4cube(orc):
+    P.pin_euclid_brute_force(orc, P.all_pairs(4))
+
+
+def test_euclid_brute_force_random(orc):
+    rng = np.random.default_rng(31)
+    P.pin_euclid_brute_force(orc, P.random_pairs(rng, 800, 14))
+
+
+def test_euclid_closed_forms(orc):
+    P.pin_euclid_closed_forms(orc)
+
+
+def test_euclid_invariants(orc):
+    P.pin_euclid_invariants(orc, workloads.config1().segs[:600])
+    rng = np.random.default_rng(32)
+    P.pin_euclid_invariants(orc, workloads.uniform_segments(rng, 300, (2048, 64, 3000)))
+
+
+def test_euclid_volume(orc):
+    rng = np.random.default_rng(33)
+    dims = (40, 23, 17)
+    P.pin_euclid_volume(orc, workloads.uniform_segments(rng, 400, dims), dims)

@@ -25,8 +25,8 @@ MUTANTS = [
      "if (g < cap)\n                oracle_voxel(seg, k, xyz + 3 * g);",
      "if (k == 0) continue;\n            if (g < cap)\n                oracle_voxel(seg, k, xyz + 3 * g);"),
     ("32-bit list drops the start voxel",
-     "if (g < cap)\n                out[g] = (uint32_t)v[0]",
-     "if (k == 0) continue;\n            if (g < cap)\n                out[g] = (uint32_t)v[0]"),
+     "if (g < cap) out[g] = pack32(v);",
+     "if (k == 0) continue;\n            if (g < cap) out[g] = pack32(v);"),
     ("y and z swapped in the 32-bit word", "((uint32_t)v[1] << 10) | ((uint32_t)v[2] << 20)",
      "((uint32_t)v[2] << 10) | ((uint32_t)v[1] << 20)"),
     ("wrong 64-bit field width", "((uint64_t)v[1] << 21) | ((uint64_t)v[2] << 42)",
@@ -39,6 +39,13 @@ MUTANTS = [
     ("upper bound inclusive", "v >= dims[c % 3]", "v > dims[c % 3]"),
     ("W taken from E instead of E - S", "(__int128)(E - S) * k", "(__int128)(E) * k"),
     ("bit order reversed in the word", "(uint32_t)1 << (lin % 32)", "(uint32_t)0x80000000u >> (lin % 32)"),
+    ("Euclidean length rounded up", "    return oracle_isqrt(sq);", "    return oracle_isqrt(sq) + (oracle_isqrt(sq) * oracle_isqrt(sq) < sq);"),
+    ("square root digit step dropped", "            r = (r >> 1) + bit;", "            r = (r >> 1);"),
+    ("repeated voxels kept", "if (k > 0 && v[0] == prev[0] && v[1] == prev[1] && v[2] == prev[2]) continue;",
+     "if (0) continue;"),
+    ("repeat test on x only", "if (k > 0 && v[0] == prev[0] && v[1] == prev[1] && v[2] == prev[2]) continue;",
+     "if (k > 0 && v[0] == prev[0]) continue;"),
+    ("variant uses N = max|d|", "    return oracle_isqrt(sq);", "    return oracle_steps(seg);"),
 ]
 
 
@@ -56,6 +63,10 @@ def _pins(O):
         ("carry", lambda: P.pin_carry_recurrence(O, P.random_pairs(rng, 50, 40))),
         ("invariants", lambda: P.pin_invariants(O, workloads.config1().segs[:300], (256, 256, 256))),
         ("outputs", lambda: P.pin_outputs_agree(O, workloads.uniform_segments(rng, 50, (13, 7, 5)), (13, 7, 5))),
+        ("euclid_hand", lambda: P.pin_euclid_hand(O)),
+        ("euclid_isqrt", lambda: P.pin_euclid_isqrt(O)),
+        ("euclid_brute_force", lambda: P.pin_euclid_brute_force(O, P.all_pairs(3))),
+        ("euclid_invariants", lambda: P.pin_euclid_invariants(O, workloads.config1().segs[:100])),
     ]
     for name, fn in checks:
         try:
