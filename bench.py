@@ -565,6 +565,35 @@ def run_ours(args):
                            "vox_unbrick back to row-major, checked equal to the row-major volume"}
         del bmask
 
+    # the Euclidean-N variant of Eq. (1)-(2) (repeats dropped) on the same batch:
+    # one vox_euclid_generate (sample scan, run counts, run scan, compacted list32
+    # + volume by atomics)
+    euclid = None
+    if not args.no_euclid:
+        ews = torch.empty(vox.vox_euclid_workspace_size(n), dtype=torch.uint8, device=dev)
+        Vd, Vs = vox.vox_euclid_plan(segs, w.dims, ews, status)
+        elst = torch.empty(Vd, dtype=torch.int32, device=dev)
+        emask = torch.empty(words, dtype=torch.int32, device=dev)
+        te = []
+        for i in range(min(args.steps, 20) + 3):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            vox.vox_euclid_generate(segs, w.dims, ews, status, elst, emask, vox.OUT_LIST32 | vox.OUT_BITMASK |
+                                    vox.OUT_FRESH, None, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if i >= 3:
+                te.append(e0.elapsed_time(e1))
+        if int(status.item()) != 0:
+            raise RuntimeError(f"device status {vox.strerror(int(status.item()))}")
+        ems = float(np.mean(te))
+        euclid = {"ms": ems, "voxels": Vd, "samples": Vs, "voxels_per_s": Vd / ems * 1e3,
+                  "samples_per_s": Vs / ems * 1e3,
+                  "note": "N = int(|E - S|); one vox_euclid_generate call: list32 (compacted) + fresh volume "
+                          "(per-voxel atomics); L2 flushed between calls"}
+        del ews, elst, emask
+
     # end to end through the host-buffer entry point (copies inside the timed region)
     e2e = None
     if not args.no_e2e:
@@ -634,6 +663,7 @@ def run_ours(args):
         "wall_s_eager_region": wall,
         "roofline": roofline, "roofline_other": roofline_other, "cpu_baseline": cpu, "e2e": e2e,
         "batched_vs_plain": batched, "serving": served, "sweeps": sweeps, "bricked_volume": bricked,
+        "euclid_variant": euclid,
         "clocks": clocks,
         "gpu_launches": 7 * args.steps,
         "gpu_launches_note": "graph-timed region, per step: k_scan<true>, k_bin_count, k_generate (list), "
@@ -658,6 +688,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-sweeps", action="store_true")
+    ap.add_argument("--no-euclid", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()

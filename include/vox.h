@@ -161,6 +161,36 @@ vox_status vox_generate_from_scan(const vox_segment *d_segs, int64_t n, vox_dims
                                   void *stream);
 
 /*
+ * The Euclidean-N variant (Section 3, Eq. (1)-(2) read literally): N =
+ * int(|E - S|), the integer part of the Euclidean length, instead of
+ * max |d_a|; samples G_k = S + W k, W = (E - S) / N, k = 0..N, each mapped to
+ * its nearest lattice point with the same rounding (ties away from S). Since N
+ * can exceed max |d_a|, consecutive samples can share a voxel; a voxel equal to
+ * the previous sample's is not added again (the voxel set of Fig. 3). The
+ * output of a segment is therefore between max|d_a| + 1 and N + 1 voxels, not
+ * known before the call: vox_euclid_plan returns the total for sizing.
+ *   vox_euclid_workspace_size  workspace bytes for n segments (the sample scan
+ *                              plus max(n, 2^20) run slots, 12 B each)
+ *   vox_euclid_generate        as vox_generate (same outputs and flags except
+ *                              VOX_OUT_BRICKED; the volume by per-voxel atomics),
+ *                              asynchronous; d_offsets: device int64[n + 1] that
+ *                              receives each segment's first list position and
+ *                              the total at [n], or NULL. A list capacity below
+ *                              the total is VOX_ERR_CAPACITY (device), nothing
+ *                              written.
+ *   vox_euclid_plan            SYNCHRONOUS: the total voxel count (*h_voxels) and
+ *                              the total sample count (*h_samples), either may
+ *                              be NULL; returns the device status (e.g.
+ *                              VOX_ERR_OUT_OF_BOUNDS).
+ */
+size_t vox_euclid_workspace_size(int64_t n);
+vox_status vox_euclid_generate(const vox_segment *d_segs, int64_t n, vox_dims dims, void *d_list,
+                               int64_t list_capacity, uint32_t *d_mask, int flags, int64_t *d_offsets, void *d_ws,
+                               size_t ws_bytes, int32_t *d_status, void *stream);
+vox_status vox_euclid_plan(const vox_segment *d_segs, int64_t n, vox_dims dims, void *d_ws, size_t ws_bytes,
+                           int32_t *d_status, int64_t *h_voxels, int64_t *h_samples, void *stream);
+
+/*
  * Brick-major volumes (VOX_OUT_BRICKED). The brick geometry depends on dims only:
  * B0 = the largest 32 * 2^k not above min(w, 256), then B1 x B2 power-of-two
  * rows (B1 = 2 B2 or B2) with B0/32 * B1 * B2 <= 32768 words; w % 32 == 0.

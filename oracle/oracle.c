@@ -295,7 +295,7 @@ static int64_t euclid_segment(const int32_t *seg, oracle_emit_fn emit, void *ctx
     int64_t added = 0;
     for (int64_t k = 0; k <= N; ++k) {
         int64_t v[3];
-        oracle_euclid_voxel(seg, k, v);
+        voxel_of_sample(seg, k, N, v);
         if (k > 0 && v[0] == prev[0] && v[1] == prev[1] && v[2] == prev[2]) continue;
         if (emit) emit(ctx, v);
         prev[0] = v[0];

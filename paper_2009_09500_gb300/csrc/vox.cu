@@ -17,6 +17,7 @@
 #include "vox.h"
 #include "vox_bricks.cuh"
 #include "vox_kernels.cuh"
+#include "vox_euclid.cuh"
 
 namespace {
 
@@ -269,13 +270,13 @@ bool uses_bricks(int64_t n, vox_dims dims, size_t ws_bytes, BrickGeom *G)
 vox_status launch_count_scan(const vox_segment *segs, int64_t n, vox_dims dims, int32_t *counts,
                              int64_t *offsets_out, void *ws, size_t ws_bytes, int32_t *status, cudaStream_t stream,
                              const SceneDesc *scenes = nullptr, const int32_t *scene_of = nullptr,
-                             int32_t n_scenes = 0)
+                             int32_t n_scenes = 0, bool euclid = false)
 {
     const WsLayout L = ws_layout(n);
     char *base = static_cast<char *>(ws);
     if (cudaMemsetAsync(base, 0, L.offsets, stream) != cudaSuccess) return VOX_ERR_CUDA;
     BrickGeom G;
-    const bool bins = scene_of == nullptr && uses_bricks(n, dims, ws_bytes, &G);
+    const bool bins = !euclid && scene_of == nullptr && uses_bricks(n, dims, ws_bytes, &G);
     VolLayout VL{};
     if (bins) {
         VL = vol_layout(n, G, 0);
@@ -301,7 +302,8 @@ vox_status launch_count_scan(const vox_segment *segs, int64_t n, vox_dims dims, 
     p.scenes = scenes;
     p.scene_of = scene_of;
     p.n_scenes = n_scenes;
-    k_scan<true><<<static_cast<unsigned>(L.n_tiles), kScanThreads, 0, stream>>>(p);
+    if (euclid) k_scan<true, true><<<static_cast<unsigned>(L.n_tiles), kScanThreads, 0, stream>>>(p);
+    else k_scan<true><<<static_cast<unsigned>(L.n_tiles), kScanThreads, 0, stream>>>(p);
     if (bins) {
         BinParams bp{};
         bp.segs = p.segs;
@@ -564,6 +566,107 @@ vox_status noalloc_scratch(void **out)
     return VOX_OK;
 }
 
+// ---- the Euclidean-N variant ---------------------------------------------------
+// Workspace: the count + scan layout of the samples, then the run arrays.
+struct EuclidLayout {
+    int64_t n_runs;   // run slots
+    int64_t n_tiles;  // scan tiles over the run counts
+    size_t hdr;       // ticket of the run scan
+    size_t count;     // int32 [n_runs]
+    size_t desc;      // uint64 [n_tiles]
+    size_t off;       // int64 [n_runs + 4]
+    size_t total;
+};
+
+EuclidLayout euclid_layout(int64_t n)
+{
+    EuclidLayout E;
+    E.n_runs = std::max<int64_t>(n, kEuclidRunSlots);
+    E.n_tiles = (E.n_runs + kScanTile - 1) / kScanTile;
+    E.hdr = ws_layout(n).total;
+    E.count = E.hdr + kWsAlign;
+    E.desc = E.count + align_up(4 * static_cast<size_t>(E.n_runs));
+    E.off = E.desc + align_up(8 * static_cast<size_t>(E.n_tiles));
+    E.total = E.off + align_up(8 * static_cast<size_t>(E.n_runs + 4));
+    return E;
+}
+
+template <bool kWrite, int OUT, bool LIN64>
+vox_status launch_euclid_runs(const EuclidParams &p, cudaStream_t stream)
+{
+    const int sms = sm_count();
+    if (sms <= 0) return VOX_ERR_CUDA;
+    const int64_t want = (p.n_runs + 255) / 256;
+    const unsigned blocks = static_cast<unsigned>(std::min<int64_t>(want, static_cast<int64_t>(sms) * 8));
+    k_euclid_runs<kWrite, OUT, LIN64><<<blocks, 256, 0, stream>>>(p);
+    return cudaGetLastError() == cudaSuccess ? VOX_OK : VOX_ERR_CUDA;
+}
+
+// Count + scan of the samples, voxels per run, scan of the run counts, and
+// (unless count_only) the compacted outputs.
+vox_status launch_euclid(const vox_segment *segs, int64_t n, vox_dims dims, void *list, int64_t capacity,
+                         uint32_t *mask, int flags, int64_t *seg_off, void *ws, int32_t *status,
+                         cudaStream_t stream, bool count_only)
+{
+    const EuclidLayout E = euclid_layout(n);
+    char *base = static_cast<char *>(ws);
+    if (vox_status e = launch_count_scan(segs, n, dims, nullptr, nullptr, ws, ws_layout(n).total, status, stream,
+                                         nullptr, nullptr, 0, true))
+        return e;
+    if (cudaMemsetAsync(base + E.hdr, 0, kWsAlign, stream) != cudaSuccess) return VOX_ERR_CUDA;
+    if (cudaMemsetAsync(base + E.desc, 0, E.off - E.desc, stream) != cudaSuccess) return VOX_ERR_CUDA;
+    EuclidParams p;
+    p.segs = reinterpret_cast<const int32_t *>(segs);
+    p.n = n;
+    p.offsets = reinterpret_cast<const int64_t *>(base + ws_layout(n).offsets);
+    p.w = dims.w;
+    p.h = dims.h;
+    p.n_runs = E.n_runs;
+    p.run_count = reinterpret_cast<int32_t *>(base + E.count);
+    p.run_off = reinterpret_cast<const int64_t *>(base + E.off);
+    p.list = list;
+    p.capacity = capacity;
+    p.mask = mask;
+    p.seg_off = seg_off;
+    p.status = status;
+    if (vox_status e = launch_euclid_runs<false, 0, false>(p, stream)) return e;
+    ScanParams sp{};
+    sp.counts_in = p.run_count;
+    sp.n = E.n_runs;
+    sp.offsets = reinterpret_cast<int64_t *>(base + E.off);
+    sp.desc = reinterpret_cast<uint64_t *>(base + E.desc);
+    sp.ticket = reinterpret_cast<uint32_t *>(base + E.hdr);
+    sp.status = status;
+    sp.n_tiles = E.n_tiles;
+    sp.stall_tile = -1;
+    sp.wait_ns = static_cast<uint64_t>(g_wait_ns.load());
+    k_scan<false><<<static_cast<unsigned>(E.n_tiles), kScanThreads, 0, stream>>>(sp);
+    if (cudaGetLastError() != cudaSuccess) return VOX_ERR_CUDA;
+    if (count_only) return VOX_OK;
+    const bool bm = flags & VOX_OUT_BITMASK;
+    if (bm && (flags & VOX_OUT_FRESH) &&
+        cudaMemsetAsync(mask, 0, 4 * static_cast<size_t>(vox_mask_words(dims)), stream) != cudaSuccess)
+        return VOX_ERR_CUDA;
+    const bool lin64 = volume_bits(dims) > (uint64_t(1) << 32);
+    vox_status e = VOX_OK;
+    if (flags & VOX_OUT_LIST32) {
+        e = bm ? launch_euclid_runs<true, kOutList32 | kOutMask, false>(p, stream)
+               : launch_euclid_runs<true, kOutList32, false>(p, stream);
+    } else if (flags & VOX_OUT_LIST64) {
+        e = !bm ? launch_euclid_runs<true, kOutList64, false>(p, stream)
+                : (lin64 ? launch_euclid_runs<true, kOutList64 | kOutMask, true>(p, stream)
+                         : launch_euclid_runs<true, kOutList64 | kOutMask, false>(p, stream));
+    } else {
+        e = lin64 ? launch_euclid_runs<true, kOutMask, true>(p, stream)
+                  : launch_euclid_runs<true, kOutMask, false>(p, stream);
+    }
+    if (e) return e;
+    if (seg_off != nullptr && cudaMemcpyAsync(seg_off + n, base + E.off + 8 * static_cast<size_t>(E.n_runs),
+                                              sizeof(int64_t), cudaMemcpyDeviceToDevice, stream) != cudaSuccess)
+        return VOX_ERR_CUDA;
+    return VOX_OK;
+}
+
 // Bytes of the host-call arena before its workspace: status, segments, list, volume.
 size_t host_arena_prefix(int64_t n, vox_dims dims, int flags, int64_t list_capacity)
 {
@@ -758,6 +861,64 @@ vox_status vox_unbrick(const uint32_t *d_bricked, vox_dims dims, uint32_t *d_mas
     const int64_t blocks = std::min<int64_t>((rows + 7) / 8, static_cast<int64_t>(sms) * 16);
     k_unbrick<<<static_cast<unsigned>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(d_bricked, G, d_mask);
     return cudaGetLastError() == cudaSuccess ? VOX_OK : VOX_ERR_CUDA;
+}
+
+size_t vox_euclid_workspace_size(int64_t n)
+{
+    if (n < 0) return 0;
+    return euclid_layout(n).total;
+}
+
+vox_status vox_euclid_generate(const vox_segment *d_segs, int64_t n, vox_dims dims, void *d_list,
+                               int64_t list_capacity, uint32_t *d_mask, int flags, int64_t *d_offsets, void *d_ws,
+                               size_t ws_bytes, int32_t *d_status, void *stream)
+{
+    if (flags & VOX_OUT_BRICKED) return VOX_ERR_INVALID_ARG;
+    if (vox_status e = check_generate_args(d_segs, n, dims, d_list, list_capacity, d_mask, flags, d_ws, ws_bytes,
+                                           d_status))
+        return e;
+    if (n >= 0 && ws_bytes < euclid_layout(n).total) return VOX_ERR_WORKSPACE;
+    if (d_offsets != nullptr && !aligned(d_offsets, 8)) return VOX_ERR_ALIGNMENT;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), s) != cudaSuccess) return VOX_ERR_CUDA;
+    if (n == 0) {
+        if ((flags & VOX_OUT_BITMASK) && (flags & VOX_OUT_FRESH) &&
+            cudaMemsetAsync(d_mask, 0, 4 * static_cast<size_t>(vox_mask_words(dims)), s) != cudaSuccess)
+            return VOX_ERR_CUDA;
+        if (d_offsets != nullptr && cudaMemsetAsync(d_offsets, 0, sizeof(int64_t), s) != cudaSuccess)
+            return VOX_ERR_CUDA;
+        return VOX_OK;
+    }
+    return launch_euclid(d_segs, n, dims, d_list, list_capacity, d_mask, flags, d_offsets, d_ws, d_status, s, false);
+}
+
+vox_status vox_euclid_plan(const vox_segment *d_segs, int64_t n, vox_dims dims, void *d_ws, size_t ws_bytes,
+                           int32_t *d_status, int64_t *h_voxels, int64_t *h_samples, void *stream)
+{
+    if (n < 0 || d_status == nullptr || (n > 0 && d_segs == nullptr)) return VOX_ERR_INVALID_ARG;
+    if (vox_status e = check_dims(dims)) return e;
+    if (n > 0 && !aligned(d_segs, 16)) return VOX_ERR_ALIGNMENT;
+    if (d_ws == nullptr || !aligned(d_ws, kWsAlign) || ws_bytes < euclid_layout(n).total) return VOX_ERR_WORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int64_t voxels = 0, samples = 0;
+    int32_t st = 0;
+    if (n > 0) {
+        if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), s) != cudaSuccess) return VOX_ERR_CUDA;
+        if (vox_status e = launch_euclid(d_segs, n, dims, nullptr, 0, nullptr, 0, nullptr, d_ws, d_status, s, true))
+            return e;
+        const EuclidLayout E = euclid_layout(n);
+        const char *base = static_cast<const char *>(d_ws);
+        if (cudaMemcpyAsync(&samples, base + ws_layout(n).offsets + 8 * static_cast<size_t>(n), 8,
+                            cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaMemcpyAsync(&voxels, base + E.off + 8 * static_cast<size_t>(E.n_runs), 8, cudaMemcpyDeviceToHost,
+                            s) != cudaSuccess ||
+            cudaMemcpyAsync(&st, d_status, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return VOX_ERR_CUDA;
+    }
+    if (h_voxels) *h_voxels = voxels;
+    if (h_samples) *h_samples = samples;
+    return static_cast<vox_status>(st);
 }
 
 size_t vox_workspace_size_volume(int64_t n, vox_dims dims, int64_t piece_capacity)

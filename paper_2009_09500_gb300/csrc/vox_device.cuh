@@ -240,4 +240,25 @@ struct Stepper {
     }
 };
 
+// int(|d|) for |d|^2 = x < 2^45: a double square root, then corrected with
+// integer comparisons so that r * r <= x < (r + 1)^2 exactly (the N of Eq. (1)).
+__device__ __forceinline__ int32_t isqrt_i64(int64_t x)
+{
+    int64_t r = static_cast<int64_t>(sqrt(static_cast<double>(x)));
+    while (r > 0 && r * r > x) --r;
+    while ((r + 1) * (r + 1) <= x) ++r;
+    return static_cast<int32_t>(r);
+}
+
+__device__ __forceinline__ int32_t euclid_steps(const int32_t *rec)
+{
+    int64_t s = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int64_t d = static_cast<int64_t>(rec[3 + a]) - rec[a];
+        s += d * d;
+    }
+    return isqrt_i64(s);
+}
+
 }  // namespace vox

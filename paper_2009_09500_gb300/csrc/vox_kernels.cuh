@@ -75,7 +75,9 @@ struct ScanParams {
 // ---------------------------------------------------------------- count + scan
 // kFromSegments: the counts are N + 1 of each segment (with endpoint checks);
 // otherwise they are read from p.counts_in (e.g. pieces per brick).
-template <bool kFromSegments>
+// kEuclid: the count of a segment is its sample count with the Euclidean N of
+// Eq. (1), int(|E - S|) + 1.
+template <bool kFromSegments, bool kEuclid = false>
 __global__ void __launch_bounds__(kScanThreads) k_scan(ScanParams p)
 {
     __shared__ __align__(16) int32_t s_cnt[kScanTile];
@@ -121,7 +123,12 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(ScanParams p)
                             (unsigned)y0 < (unsigned)H && (unsigned)y1 < (unsigned)H &&
                             (unsigned)z0 < (unsigned)D && (unsigned)z1 < (unsigned)D;
             if (ok) {
-                c = max(abs(x1 - x0), max(abs(y1 - y0), abs(z1 - z0))) + 1;
+                if constexpr (kEuclid) {
+                    const int32_t rec[6] = {x0, y0, z0, x1, y1, z1};
+                    c = euclid_steps(rec) + 1;
+                } else {
+                    c = max(abs(x1 - x0), max(abs(y1 - y0), abs(z1 - z0))) + 1;
+                }
             } else {
                 bad = true;
                 c = 1;

@@ -42,6 +42,7 @@ EXPORTED = (
     "vox_workspace_size_volume", "vox_plan", "vox_workspace_size_batched", "vox_generate_batched",
     "vox_set_tuning", "vox_get_tuning", "vox_host_arena_size_volume",
     "vox_mask_words_bricked", "vox_brick_shape", "vox_unbrick",
+    "vox_euclid_workspace_size", "vox_euclid_generate", "vox_euclid_plan",
 )
 
 VOLUME_AUTO = 0
@@ -103,6 +104,12 @@ def load(path: str | None = None):
     lib.vox_brick_shape.restype = i32
     lib.vox_unbrick.argtypes = [vp, Dims, vp, vp]
     lib.vox_unbrick.restype = i32
+    lib.vox_euclid_workspace_size.argtypes = [i64]
+    lib.vox_euclid_workspace_size.restype = sz
+    lib.vox_euclid_generate.argtypes = [vp, i64, Dims, vp, i64, vp, i32, vp, vp, sz, vp, vp]
+    lib.vox_euclid_generate.restype = i32
+    lib.vox_euclid_plan.argtypes = [vp, i64, Dims, vp, sz, vp, vp, vp, vp]
+    lib.vox_euclid_plan.restype = i32
     lib.vox_generate_host.argtypes = [vp, i64, Dims, vp, i64, vp, i32, vp, sz, vp, vp]
     lib.vox_generate_host.restype = i32
     lib.vox_strerror.argtypes = [i32]
@@ -303,6 +310,39 @@ def vox_unbrick(bricked, dims, mask, stream=None):
     st = load().vox_unbrick(_ptr(bricked), _dims(dims), _ptr(mask), _stream(stream))
     if st != OK:
         raise VoxError(st, "vox_unbrick")
+
+
+def vox_euclid_workspace_size(n: int) -> int:
+    return int(load().vox_euclid_workspace_size(int(n)))
+
+
+def vox_euclid_plan(segs, dims, ws, status, stream=None):
+    """(total voxels, total samples) of the Euclidean-N variant (synchronous)."""
+    v, s = ctypes.c_int64(0), ctypes.c_int64(0)
+    st = load().vox_euclid_plan(_ptr(segs), segs.shape[0], _dims(dims), _ptr(ws), ws.numel(), _ptr(status),
+                                ctypes.byref(v), ctypes.byref(s), _stream(stream))
+    if st != OK:
+        raise VoxError(st, "vox_euclid_plan")
+    return int(v.value), int(s.value)
+
+
+def vox_euclid_generate(segs, dims, ws, status, list_out=None, mask=None, flags=None, offsets=None, stream=None,
+                        capacity=None):
+    """The Euclidean-N variant: compacted list and/or volume (asynchronous).
+    offsets: device int64 [n + 1] receiving each segment's first list position."""
+    import torch
+
+    if flags is None:
+        flags = 0
+        if list_out is not None:
+            flags |= OUT_LIST64 if list_out.dtype in (torch.int64, torch.uint64) else OUT_LIST32
+        if mask is not None:
+            flags |= OUT_BITMASK
+    cap = (list_out.numel() if list_out is not None else 0) if capacity is None else int(capacity)
+    st = load().vox_euclid_generate(_ptr(segs), segs.shape[0], _dims(dims), _ptr(list_out), cap, _ptr(mask),
+                                    int(flags), _ptr(offsets), _ptr(ws), ws.numel(), _ptr(status), _stream(stream))
+    if st != OK:
+        raise VoxError(st, "vox_euclid_generate")
 
 
 def vox_host_arena_size_volume(n: int, dims, flags: int, capacity: int, piece_capacity: int) -> int:
