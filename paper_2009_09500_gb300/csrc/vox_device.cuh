@@ -240,11 +240,13 @@ struct Stepper {
     }
 };
 
-// int(|d|) for |d|^2 = x < 2^45: a double square root, then corrected with
-// integer comparisons so that r * r <= x < (r + 1)^2 exactly (the N of Eq. (1)).
+// int(|d|) for |d|^2 = x < 2^45: a single-precision square root (within a few
+// units of the answer for r < 2^22; double precision is a slow pipe on this
+// GPU), then corrected with integer comparisons so that r * r <= x < (r + 1)^2
+// exactly (the N of Eq. (1)).
 __device__ __forceinline__ int32_t isqrt_i64(int64_t x)
 {
-    int64_t r = static_cast<int64_t>(sqrt(static_cast<double>(x)));
+    int64_t r = static_cast<int64_t>(sqrtf(static_cast<float>(x)));
     while (r > 0 && r * r > x) --r;
     while ((r + 1) * (r + 1) <= x) ++r;
     return static_cast<int32_t>(r);

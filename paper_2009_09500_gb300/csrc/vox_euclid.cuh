@@ -134,6 +134,20 @@ __global__ void __launch_bounds__(256) k_euclid_runs(EuclidParams p)
             const int2 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
             rec[0] = a.x; rec[1] = a.y; rec[2] = b.x; rec[3] = b.y; rec[4] = c.x; rec[5] = c.y;
         }
+        // the next segment's record and end, loaded ahead so that crossing into it
+        // does not wait on memory (segment n - 1 has no successor: nothing loaded)
+        int2 na = make_int2(0, 0), nb = na, nc = na;
+        int64_t next_end = seg_end;
+        auto prefetch = [&](int64_t t) {
+            if (t + 1 < p.n && seg_end < g1) {
+                const int2 *q = reinterpret_cast<const int2 *>(p.segs + 6 * (t + 1));
+                na = __ldg(q);
+                nb = __ldg(q + 1);
+                nc = __ldg(q + 2);
+                next_end = __ldg(p.offsets + t + 2);
+            }
+        };
+        prefetch(s);
         const int32_t k0 = static_cast<int32_t>(g0 - __ldg(p.offsets + s));
         EuclidStepper<PackT, LinT> st;
         bool add, first;
@@ -152,10 +166,9 @@ __global__ void __launch_bounds__(256) k_euclid_runs(EuclidParams p)
         for (int64_t g = g0; g < g1; ++g) {
             if (g == seg_end) {  // the next segment starts here
                 ++s;
-                seg_end = __ldg(p.offsets + s + 1);
-                const int2 *q = reinterpret_cast<const int2 *>(p.segs + 6 * s);
-                const int2 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
-                rec[0] = a.x; rec[1] = a.y; rec[2] = b.x; rec[3] = b.y; rec[4] = c.x; rec[5] = c.y;
+                seg_end = next_end;
+                rec[0] = na.x; rec[1] = na.y; rec[2] = nb.x; rec[3] = nb.y; rec[4] = nc.x; rec[5] = nc.y;
+                prefetch(s);
                 st.enter(rec, 0, w, wh);
                 add = first = true;
             }
