@@ -570,8 +570,9 @@ def run_ours(args):
     # + volume by atomics)
     euclid = None
     if not args.no_euclid:
-        ews = torch.empty(vox.vox_euclid_workspace_size(n), dtype=torch.uint8, device=dev)
-        Vd, Vs = vox.vox_euclid_plan(segs, w.dims, ews, status)
+        ews = torch.empty(vox.vox_euclid_workspace_size_volume(n, w.dims, 0), dtype=torch.uint8, device=dev)
+        Vd, Vs, EP = vox.vox_euclid_plan(segs, w.dims, ews, status, with_pieces=True)
+        ews = torch.empty(vox.vox_euclid_workspace_size_volume(n, w.dims, EP), dtype=torch.uint8, device=dev)
         elst = torch.empty(Vd, dtype=torch.int32, device=dev)
         emask = torch.empty(words, dtype=torch.int32, device=dev)
         te = []
@@ -588,10 +589,10 @@ def run_ours(args):
         if int(status.item()) != 0:
             raise RuntimeError(f"device status {vox.strerror(int(status.item()))}")
         ems = float(np.mean(te))
-        euclid = {"ms": ems, "voxels": Vd, "samples": Vs, "voxels_per_s": Vd / ems * 1e3,
+        euclid = {"ms": ems, "voxels": Vd, "samples": Vs, "pieces": EP, "voxels_per_s": Vd / ems * 1e3,
                   "samples_per_s": Vs / ems * 1e3,
-                  "note": "N = int(|E - S|); one vox_euclid_generate call: list32 (compacted) + fresh volume "
-                          "(per-voxel atomics); L2 flushed between calls"}
+                  "note": "N = int(|E - S|); one vox_euclid_generate call: list32 (compacted, run walk) + fresh "
+                          "volume (bricks); L2 flushed between calls"}
         del ews, elst, emask
 
     # end to end through the host-buffer entry point (copies inside the timed region)

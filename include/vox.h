@@ -171,24 +171,33 @@ vox_status vox_generate_from_scan(const vox_segment *d_segs, int64_t n, vox_dims
  * known before the call: vox_euclid_plan returns the total for sizing.
  *   vox_euclid_workspace_size  workspace bytes for n segments (the sample scan
  *                              plus max(n, 2^20) run slots, 12 B each)
+ *   vox_euclid_workspace_size_volume  the same followed by the brick arrays and
+ *                              room for piece_capacity pieces (e.g. *h_pieces of
+ *                              vox_euclid_plan): with it the volume is built by
+ *                              bricks (falling back to atomics on the device when
+ *                              the pieces do not fit)
  *   vox_euclid_generate        as vox_generate (same outputs and flags except
- *                              VOX_OUT_BRICKED; the volume by per-voxel atomics),
+ *                              VOX_OUT_BRICKED; the volume by bricks when the
+ *                              workspace holds them, else per-voxel atomics),
  *                              asynchronous; d_offsets: device int64[n + 1] that
  *                              receives each segment's first list position and
  *                              the total at [n], or NULL. A list capacity below
  *                              the total is VOX_ERR_CAPACITY (device), nothing
  *                              written.
- *   vox_euclid_plan            SYNCHRONOUS: the total voxel count (*h_voxels) and
- *                              the total sample count (*h_samples), either may
- *                              be NULL; returns the device status (e.g.
- *                              VOX_ERR_OUT_OF_BOUNDS).
+ *   vox_euclid_plan            SYNCHRONOUS: the total voxel count (*h_voxels),
+ *                              the total sample count (*h_samples) and the brick
+ *                              pieces (*h_pieces, 0 unless the workspace holds the
+ *                              brick arrays), each may be NULL; returns the
+ *                              device status (e.g. VOX_ERR_OUT_OF_BOUNDS).
  */
 size_t vox_euclid_workspace_size(int64_t n);
+size_t vox_euclid_workspace_size_volume(int64_t n, vox_dims dims, int64_t piece_capacity);
 vox_status vox_euclid_generate(const vox_segment *d_segs, int64_t n, vox_dims dims, void *d_list,
                                int64_t list_capacity, uint32_t *d_mask, int flags, int64_t *d_offsets, void *d_ws,
                                size_t ws_bytes, int32_t *d_status, void *stream);
 vox_status vox_euclid_plan(const vox_segment *d_segs, int64_t n, vox_dims dims, void *d_ws, size_t ws_bytes,
-                           int32_t *d_status, int64_t *h_voxels, int64_t *h_samples, void *stream);
+                           int32_t *d_status, int64_t *h_voxels, int64_t *h_samples, int64_t *h_pieces,
+                           void *stream);
 
 /*
  * Brick-major volumes (VOX_OUT_BRICKED). The brick geometry depends on dims only:

@@ -242,13 +242,39 @@ struct VolLayout {
     size_t total;
 };
 
-// The volume path's workspace follows the base layout of ws_layout(n).
-VolLayout vol_layout(int64_t n, const BrickGeom &G, int64_t capacity)
+// ---- the Euclidean-N variant ---------------------------------------------------
+// Workspace: the count + scan layout of the samples, then the run arrays.
+struct EuclidLayout {
+    int64_t n_runs;   // run slots
+    int64_t n_tiles;  // scan tiles over the run counts
+    size_t hdr;       // ticket of the run scan
+    size_t count;     // int32 [n_runs]
+    size_t desc;      // uint64 [n_tiles]
+    size_t off;       // int64 [n_runs + 4]
+    size_t total;
+};
+
+EuclidLayout euclid_layout(int64_t n)
+{
+    EuclidLayout E;
+    E.n_runs = std::max<int64_t>(n, kEuclidRunSlots);
+    E.n_tiles = (E.n_runs + kScanTile - 1) / kScanTile;
+    E.hdr = ws_layout(n).total;
+    E.count = E.hdr + kWsAlign;
+    E.desc = E.count + align_up(4 * static_cast<size_t>(E.n_runs));
+    E.off = E.desc + align_up(8 * static_cast<size_t>(E.n_tiles));
+    E.total = E.off + align_up(8 * static_cast<size_t>(E.n_runs + 4));
+    return E;
+}
+
+// The volume path's workspace follows the base layout of ws_layout(n) (base 0),
+// or another layout ending at `base` (the Euclidean variant's run arrays).
+VolLayout vol_layout(int64_t n, const BrickGeom &G, int64_t capacity, size_t base = 0)
 {
     VolLayout L;
     const size_t nb = static_cast<size_t>(G.n_slots);
     L.n_tiles = (G.n_slots + kScanTile - 1) / kScanTile;
-    L.hdr = ws_layout(n).total;
+    L.hdr = base != 0 ? base : ws_layout(n).total;
     L.count = L.hdr + kWsAlign;
     L.desc = L.count + align_up(4 * nb);
     L.off = L.desc + align_up(8 * static_cast<size_t>(L.n_tiles));
@@ -260,9 +286,9 @@ VolLayout vol_layout(int64_t n, const BrickGeom &G, int64_t capacity)
 
 // Whether a call on n segments with this workspace builds the volume by brick
 // ownership (the workspace holds the brick arrays and room for a piece).
-bool uses_bricks(int64_t n, vox_dims dims, size_t ws_bytes, BrickGeom *G)
+bool uses_bricks(int64_t n, vox_dims dims, size_t ws_bytes, BrickGeom *G, size_t base = 0)
 {
-    return n > 0 && make_geom(dims, G) && ws_bytes >= vol_layout(n, *G, 1).total;
+    return n > 0 && make_geom(dims, G) && ws_bytes >= vol_layout(n, *G, 1, base).total;
 }
 
 // Count + scan. With a brick workspace it also zeroes the brick arrays and
@@ -276,10 +302,11 @@ vox_status launch_count_scan(const vox_segment *segs, int64_t n, vox_dims dims, 
     char *base = static_cast<char *>(ws);
     if (cudaMemsetAsync(base, 0, L.offsets, stream) != cudaSuccess) return VOX_ERR_CUDA;
     BrickGeom G;
-    const bool bins = !euclid && scene_of == nullptr && uses_bricks(n, dims, ws_bytes, &G);
+    const size_t vbase = euclid ? euclid_layout(n).total : 0;
+    const bool bins = scene_of == nullptr && uses_bricks(n, dims, ws_bytes, &G, vbase);
     VolLayout VL{};
     if (bins) {
-        VL = vol_layout(n, G, 0);
+        VL = vol_layout(n, G, 0, vbase);
         if (cudaMemsetAsync(base + VL.hdr, 0, VL.off - VL.hdr, stream) != cudaSuccess) return VOX_ERR_CUDA;
     }
     ScanParams p;
@@ -312,7 +339,8 @@ vox_status launch_count_scan(const vox_segment *segs, int64_t n, vox_dims dims, 
         bp.brick_count = reinterpret_cast<int32_t *>(base + VL.count);
         bp.status = status;
         const unsigned blocks = static_cast<unsigned>((n + 255) / 256);
-        k_bin_count<<<blocks, 256, 0, stream>>>(bp);
+        if (euclid) k_bin_count<true><<<blocks, 256, 0, stream>>>(bp);
+        else k_bin_count<false><<<blocks, 256, 0, stream>>>(bp);
     }
     return cudaGetLastError() == cudaSuccess ? VOX_OK : VOX_ERR_CUDA;
 }
@@ -399,12 +427,12 @@ vox_status launch_generate(const vox_segment *segs, int64_t n, vox_dims dims, vo
 // runs if the pieces did not fit in the workspace
 vox_status launch_bricks(const vox_segment *segs, int64_t n, const BrickGeom &G, vox_dims dims, uint32_t *mask,
                          void *ws, size_t ws_bytes, int32_t *status, cudaStream_t stream, bool count_only = false,
-                         bool fresh = false, bool bricked = false)
+                         bool fresh = false, bool bricked = false, bool euclid = false)
 {
     // the brick counts come from the count + scan (k_bin_count); the
     // tickets and look-back flags of this pass are reset here, so that the pass
     // can run again on the same counts
-    const VolLayout VL = vol_layout(n, G, 0);
+    const VolLayout VL = vol_layout(n, G, 0, euclid ? euclid_layout(n).total : 0);
     const int64_t capacity = static_cast<int64_t>((ws_bytes - VL.pieces) / 8);
     char *base = static_cast<char *>(ws);
     if (cudaMemsetAsync(base + VL.hdr, 0, kWsAlign, stream) != cudaSuccess) return VOX_ERR_CUDA;
@@ -442,7 +470,8 @@ vox_status launch_bricks(const vox_segment *segs, int64_t n, const BrickGeom &G,
     sp.n_scenes = 0;
     k_scan<false><<<static_cast<unsigned>(VL.n_tiles), kScanThreads, 0, stream>>>(sp);
     if (count_only) return cudaGetLastError() == cudaSuccess ? VOX_OK : VOX_ERR_CUDA;
-    k_bin_scatter<<<static_cast<unsigned>(bin_blocks), 256, 0, stream>>>(bp);
+    if (euclid) k_bin_scatter<true><<<static_cast<unsigned>(bin_blocks), 256, 0, stream>>>(bp);
+    else k_bin_scatter<false><<<static_cast<unsigned>(bin_blocks), 256, 0, stream>>>(bp);
     BrickParams brp;
     brp.segs = bp.segs;
     brp.G = G;
@@ -458,12 +487,16 @@ vox_status launch_bricks(const vox_segment *segs, int64_t n, const BrickGeom &G,
     brp.fresh = (fresh || bricked) ? 1 : 0;
     brp.bricked = bricked ? 1 : 0;
     const size_t bsmem = sizeof(BrickSmem);
-    if (vox_status e = allow_smem(reinterpret_cast<const void *>(k_brick_volume), bsmem)) return e;
-    const int bgrid = grid_ctas(reinterpret_cast<const void *>(k_brick_volume), kBrickThreads, bsmem);
+    const void *bk = euclid ? reinterpret_cast<const void *>(k_brick_volume<true>)
+                            : reinterpret_cast<const void *>(k_brick_volume<false>);
+    if (vox_status e = allow_smem(bk, bsmem)) return e;
+    const int bgrid = grid_ctas(bk, kBrickThreads, bsmem);
     if (bgrid <= 0) return VOX_ERR_CUDA;
-    k_brick_volume<<<static_cast<unsigned>(bgrid), kBrickThreads, bsmem, stream>>>(brp, tmap);
+    if (euclid) k_brick_volume<true><<<static_cast<unsigned>(bgrid), kBrickThreads, bsmem, stream>>>(brp, tmap);
+    else k_brick_volume<false><<<static_cast<unsigned>(bgrid), kBrickThreads, bsmem, stream>>>(brp, tmap);
     if (cudaGetLastError() != cudaSuccess) return VOX_ERR_CUDA;
     if (bricked) return VOX_OK;  // no atomics fallback for the brick-major layout (pieces must fit)
+    if (euclid) return VOX_OK;   // the variant's own atomics pass is the fallback (launched by the caller)
     return launch_generate(segs, n, dims, nullptr, 0, mask, VOX_OUT_BITMASK, ws, status, stream,
                            bp.brick_off + G.n_slots, capacity);
 }
@@ -566,31 +599,6 @@ vox_status noalloc_scratch(void **out)
     return VOX_OK;
 }
 
-// ---- the Euclidean-N variant ---------------------------------------------------
-// Workspace: the count + scan layout of the samples, then the run arrays.
-struct EuclidLayout {
-    int64_t n_runs;   // run slots
-    int64_t n_tiles;  // scan tiles over the run counts
-    size_t hdr;       // ticket of the run scan
-    size_t count;     // int32 [n_runs]
-    size_t desc;      // uint64 [n_tiles]
-    size_t off;       // int64 [n_runs + 4]
-    size_t total;
-};
-
-EuclidLayout euclid_layout(int64_t n)
-{
-    EuclidLayout E;
-    E.n_runs = std::max<int64_t>(n, kEuclidRunSlots);
-    E.n_tiles = (E.n_runs + kScanTile - 1) / kScanTile;
-    E.hdr = ws_layout(n).total;
-    E.count = E.hdr + kWsAlign;
-    E.desc = E.count + align_up(4 * static_cast<size_t>(E.n_runs));
-    E.off = E.desc + align_up(8 * static_cast<size_t>(E.n_tiles));
-    E.total = E.off + align_up(8 * static_cast<size_t>(E.n_runs + 4));
-    return E;
-}
-
 template <bool kWrite, int OUT, bool LIN64>
 vox_status launch_euclid_runs(const EuclidParams &p, cudaStream_t stream)
 {
@@ -602,16 +610,32 @@ vox_status launch_euclid_runs(const EuclidParams &p, cudaStream_t stream)
     return cudaGetLastError() == cudaSuccess ? VOX_OK : VOX_ERR_CUDA;
 }
 
-// Count + scan of the samples, voxels per run, scan of the run counts, and
-// (unless count_only) the compacted outputs.
+template <int OUT, bool LIN64>
+vox_status launch_euclid_list(const EuclidParams &p, cudaStream_t stream)
+{
+    const int sms = sm_count();
+    if (sms <= 0) return VOX_ERR_CUDA;
+    const int64_t want = (p.n_runs + 255) / 256;
+    const unsigned blocks = static_cast<unsigned>(std::min<int64_t>(want, static_cast<int64_t>(sms) * 8));
+    k_euclid_list<OUT, LIN64><<<blocks, 256, 0, stream>>>(p);
+    return cudaGetLastError() == cudaSuccess ? VOX_OK : VOX_ERR_CUDA;
+}
+
+// Count + scan of the samples (and the brick binning's counts when the workspace
+// holds brick arrays after the run arrays), voxels per run, scan of the run
+// counts, and (unless count_only) the outputs: the compacted list by the run
+// walk, the volume by bricks (then a gated atomics pass if the pieces did not
+// fit) or by the run walk's atomics.
 vox_status launch_euclid(const vox_segment *segs, int64_t n, vox_dims dims, void *list, int64_t capacity,
-                         uint32_t *mask, int flags, int64_t *seg_off, void *ws, int32_t *status,
+                         uint32_t *mask, int flags, int64_t *seg_off, void *ws, size_t ws_bytes, int32_t *status,
                          cudaStream_t stream, bool count_only)
 {
     const EuclidLayout E = euclid_layout(n);
     char *base = static_cast<char *>(ws);
-    if (vox_status e = launch_count_scan(segs, n, dims, nullptr, nullptr, ws, ws_layout(n).total, status, stream,
-                                         nullptr, nullptr, 0, true))
+    BrickGeom G;
+    const bool bricks = uses_bricks(n, dims, ws_bytes, &G, E.total);
+    if (vox_status e = launch_count_scan(segs, n, dims, nullptr, nullptr, ws, ws_bytes, status, stream, nullptr,
+                                         nullptr, 0, true))
         return e;
     if (cudaMemsetAsync(base + E.hdr, 0, kWsAlign, stream) != cudaSuccess) return VOX_ERR_CUDA;
     if (cudaMemsetAsync(base + E.desc, 0, E.off - E.desc, stream) != cudaSuccess) return VOX_ERR_CUDA;
@@ -629,36 +653,67 @@ vox_status launch_euclid(const vox_segment *segs, int64_t n, vox_dims dims, void
     p.mask = mask;
     p.seg_off = seg_off;
     p.status = status;
-    if (vox_status e = launch_euclid_runs<false, 0, false>(p, stream)) return e;
-    ScanParams sp{};
-    sp.counts_in = p.run_count;
-    sp.n = E.n_runs;
-    sp.offsets = reinterpret_cast<int64_t *>(base + E.off);
-    sp.desc = reinterpret_cast<uint64_t *>(base + E.desc);
-    sp.ticket = reinterpret_cast<uint32_t *>(base + E.hdr);
-    sp.status = status;
-    sp.n_tiles = E.n_tiles;
-    sp.stall_tile = -1;
-    sp.wait_ns = static_cast<uint64_t>(g_wait_ns.load());
-    k_scan<false><<<static_cast<unsigned>(E.n_tiles), kScanThreads, 0, stream>>>(sp);
-    if (cudaGetLastError() != cudaSuccess) return VOX_ERR_CUDA;
-    if (count_only) return VOX_OK;
+    p.gate_total = nullptr;
+    p.gate_cap = 0;
+    // output positions (the run counts and their scan) are needed for a list,
+    // the segment offsets and the plan; a volume alone goes without them
+    const bool positions = count_only || seg_off != nullptr || (flags & (VOX_OUT_LIST32 | VOX_OUT_LIST64));
+    if (positions) {
+        if (vox_status e = launch_euclid_runs<false, 0, false>(p, stream)) return e;
+        ScanParams sp{};
+        sp.counts_in = p.run_count;
+        sp.n = E.n_runs;
+        sp.offsets = reinterpret_cast<int64_t *>(base + E.off);
+        sp.desc = reinterpret_cast<uint64_t *>(base + E.desc);
+        sp.ticket = reinterpret_cast<uint32_t *>(base + E.hdr);
+        sp.status = status;
+        sp.n_tiles = E.n_tiles;
+        sp.stall_tile = -1;
+        sp.wait_ns = static_cast<uint64_t>(g_wait_ns.load());
+        k_scan<false><<<static_cast<unsigned>(E.n_tiles), kScanThreads, 0, stream>>>(sp);
+        if (cudaGetLastError() != cudaSuccess) return VOX_ERR_CUDA;
+    }
+    if (count_only) {
+        if (bricks) return launch_bricks(segs, n, G, dims, nullptr, ws, ws_bytes, status, stream, true, false, false, true);
+        return VOX_OK;
+    }
     const bool bm = flags & VOX_OUT_BITMASK;
-    if (bm && (flags & VOX_OUT_FRESH) &&
+    const bool lin64 = volume_bits(dims) > (uint64_t(1) << 32);
+    const bool vol_by_bricks = bm && bricks;
+    const bool mask_in_walk = bm && !bricks;
+    if (mask_in_walk && (flags & VOX_OUT_FRESH) &&
         cudaMemsetAsync(mask, 0, 4 * static_cast<size_t>(vox_mask_words(dims)), stream) != cudaSuccess)
         return VOX_ERR_CUDA;
-    const bool lin64 = volume_bits(dims) > (uint64_t(1) << 32);
+    // the run walk's write pass first: a list capacity error found there keeps
+    // every later kernel (the bricks too) from writing
     vox_status e = VOX_OK;
     if (flags & VOX_OUT_LIST32) {
-        e = bm ? launch_euclid_runs<true, kOutList32 | kOutMask, false>(p, stream)
-               : launch_euclid_runs<true, kOutList32, false>(p, stream);
+        e = mask_in_walk ? launch_euclid_list<kOutList32 | kOutMask, false>(p, stream)
+                         : launch_euclid_list<kOutList32, false>(p, stream);
     } else if (flags & VOX_OUT_LIST64) {
-        e = !bm ? launch_euclid_runs<true, kOutList64, false>(p, stream)
-                : (lin64 ? launch_euclid_runs<true, kOutList64 | kOutMask, true>(p, stream)
-                         : launch_euclid_runs<true, kOutList64 | kOutMask, false>(p, stream));
-    } else {
+        e = !mask_in_walk ? launch_euclid_list<kOutList64, false>(p, stream)
+                          : (lin64 ? launch_euclid_list<kOutList64 | kOutMask, true>(p, stream)
+                                   : launch_euclid_list<kOutList64 | kOutMask, false>(p, stream));
+    } else if (mask_in_walk) {
         e = lin64 ? launch_euclid_runs<true, kOutMask, true>(p, stream)
                   : launch_euclid_runs<true, kOutMask, false>(p, stream);
+    } else if (seg_off != nullptr) {
+        e = launch_euclid_runs<true, 0, false>(p, stream);  // the segment offsets alone
+    }
+    if (e) return e;
+    if (vol_by_bricks) {
+        const bool fresh = flags & VOX_OUT_FRESH;
+        if ((e = launch_bricks(segs, n, G, dims, mask, ws, ws_bytes, status, stream, false, fresh, false, true)))
+            return e;
+        // per-voxel atomics, run only if the pieces did not fit the workspace
+        const VolLayout VL = vol_layout(n, G, 0, E.total);
+        EuclidParams g = p;
+        g.list = nullptr;
+        g.seg_off = nullptr;
+        g.gate_total = reinterpret_cast<const int64_t *>(base + VL.off) + G.n_slots;
+        g.gate_cap = static_cast<int64_t>((ws_bytes - VL.pieces) / 8);
+        e = lin64 ? launch_euclid_runs<true, kOutMask, true>(g, stream)
+                  : launch_euclid_runs<true, kOutMask, false>(g, stream);
     }
     if (e) return e;
     if (seg_off != nullptr && cudaMemcpyAsync(seg_off + n, base + E.off + 8 * static_cast<size_t>(E.n_runs),
@@ -869,6 +924,15 @@ size_t vox_euclid_workspace_size(int64_t n)
     return euclid_layout(n).total;
 }
 
+size_t vox_euclid_workspace_size_volume(int64_t n, vox_dims dims, int64_t piece_capacity)
+{
+    if (n < 0 || piece_capacity < 0) return 0;
+    BrickGeom G;
+    const size_t base = euclid_layout(n).total;
+    if (!make_geom(dims, &G)) return base;
+    return vol_layout(n, G, piece_capacity > 0 ? piece_capacity : 1, base).total;
+}
+
 vox_status vox_euclid_generate(const vox_segment *d_segs, int64_t n, vox_dims dims, void *d_list,
                                int64_t list_capacity, uint32_t *d_mask, int flags, int64_t *d_offsets, void *d_ws,
                                size_t ws_bytes, int32_t *d_status, void *stream)
@@ -889,25 +953,34 @@ vox_status vox_euclid_generate(const vox_segment *d_segs, int64_t n, vox_dims di
             return VOX_ERR_CUDA;
         return VOX_OK;
     }
-    return launch_euclid(d_segs, n, dims, d_list, list_capacity, d_mask, flags, d_offsets, d_ws, d_status, s, false);
+    return launch_euclid(d_segs, n, dims, d_list, list_capacity, d_mask, flags, d_offsets, d_ws, ws_bytes, d_status, s,
+                         false);
 }
 
 vox_status vox_euclid_plan(const vox_segment *d_segs, int64_t n, vox_dims dims, void *d_ws, size_t ws_bytes,
-                           int32_t *d_status, int64_t *h_voxels, int64_t *h_samples, void *stream)
+                           int32_t *d_status, int64_t *h_voxels, int64_t *h_samples, int64_t *h_pieces, void *stream)
 {
     if (n < 0 || d_status == nullptr || (n > 0 && d_segs == nullptr)) return VOX_ERR_INVALID_ARG;
     if (vox_status e = check_dims(dims)) return e;
     if (n > 0 && !aligned(d_segs, 16)) return VOX_ERR_ALIGNMENT;
     if (d_ws == nullptr || !aligned(d_ws, kWsAlign) || ws_bytes < euclid_layout(n).total) return VOX_ERR_WORKSPACE;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    int64_t voxels = 0, samples = 0;
+    int64_t voxels = 0, samples = 0, pieces = 0;
     int32_t st = 0;
     if (n > 0) {
         if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), s) != cudaSuccess) return VOX_ERR_CUDA;
-        if (vox_status e = launch_euclid(d_segs, n, dims, nullptr, 0, nullptr, 0, nullptr, d_ws, d_status, s, true))
+        if (vox_status e = launch_euclid(d_segs, n, dims, nullptr, 0, nullptr, 0, nullptr, d_ws, ws_bytes, d_status, s,
+                                         true))
             return e;
         const EuclidLayout E = euclid_layout(n);
         const char *base = static_cast<const char *>(d_ws);
+        BrickGeom G;
+        if (uses_bricks(n, dims, ws_bytes, &G, E.total)) {
+            const VolLayout VL = vol_layout(n, G, 0, E.total);
+            if (cudaMemcpyAsync(&pieces, base + VL.off + 8 * static_cast<size_t>(G.n_slots), 8,
+                                cudaMemcpyDeviceToHost, s) != cudaSuccess)
+                return VOX_ERR_CUDA;
+        }
         if (cudaMemcpyAsync(&samples, base + ws_layout(n).offsets + 8 * static_cast<size_t>(n), 8,
                             cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaMemcpyAsync(&voxels, base + E.off + 8 * static_cast<size_t>(E.n_runs), 8, cudaMemcpyDeviceToHost,
@@ -918,6 +991,7 @@ vox_status vox_euclid_plan(const vox_segment *d_segs, int64_t n, vox_dims dims, 
     }
     if (h_voxels) *h_voxels = voxels;
     if (h_samples) *h_samples = samples;
+    if (h_pieces) *h_pieces = pieces;
     return static_cast<vox_status>(st);
 }
 

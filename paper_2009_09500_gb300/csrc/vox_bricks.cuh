@@ -26,6 +26,7 @@
 #include <cuda.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "vox_device.cuh"
 
@@ -136,8 +137,10 @@ struct AxisCrossings {
 
 // Calls f(brick, k_lo, len) for every maximal run of consecutive steps of the
 // segment that stays in one brick, in increasing k. Endpoints must be inside
-// the volume. Brick indices fit 32 bits (at most 2^26 bricks).
-template <typename F>
+// the volume. Brick indices fit 32 bits (at most 2^26 bricks). kEuclid: the
+// steps are the samples of the Euclidean-N variant, N = int(|E - S|) (the
+// crossing formula holds for any N >= max |d_a|).
+template <bool kEuclid = false, typename F>
 __device__ __forceinline__ void for_each_piece(const int32_t *rec, const BrickGeom &G, F &&f)
 {
     AxisCrossings ax[3];
@@ -148,6 +151,7 @@ __device__ __forceinline__ void for_each_piece(const int32_t *rec, const BrickGe
         A[a] = abs(rec[3 + a] - rec[a]);
         N = max(N, A[a]);
     }
+    if constexpr (kEuclid) N = euclid_steps(rec);
     int32_t brick = (rec[0] >> G.logB[0]) + G.nb[0] * ((rec[1] >> G.logB[1]) + G.nb[1] * (rec[2] >> G.logB[2]));
     const int32_t stride[3] = {1, G.nb[0], G.nb[0] * G.nb[1]};
 #pragma unroll
@@ -205,6 +209,7 @@ __device__ __forceinline__ void load_record(const int32_t *segs, int64_t s, int3
 }
 
 // One segment per thread.
+template <bool kEuclid>
 __global__ void __launch_bounds__(256) k_bin_count(BinParams p)
 {
     const int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -213,10 +218,13 @@ __global__ void __launch_bounds__(256) k_bin_count(BinParams p)
     load_record(p.segs, s, r);
     if (!endpoints_inside(r, p.G)) return;  // reported by the count kernel
     const int32_t rep = static_cast<int32_t>(s) & (p.G.reps - 1);
-    for_each_piece(r, p.G, [&](int32_t b, int32_t, int32_t len) { atomicAdd(p.brick_count + piece_slot(p.G, b, len, rep), 1); });
+    for_each_piece<kEuclid>(r, p.G, [&](int32_t b, int32_t, int32_t len) {
+        atomicAdd(p.brick_count + piece_slot(p.G, b, len, rep), 1);
+    });
 }
 
 // One segment per thread.
+template <bool kEuclid>
 __global__ void __launch_bounds__(256) k_bin_scatter(BinParams p)
 {
     const int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -242,7 +250,7 @@ __global__ void __launch_bounds__(256) k_bin_scatter(BinParams p)
             if (e < nb) p.pieces[pos[e]] = val[e];
         nb = 0;
     };
-    for_each_piece(r, p.G, [&](int32_t b, int32_t k, int32_t len) {
+    for_each_piece<kEuclid>(r, p.G, [&](int32_t b, int32_t k, int32_t len) {
 #pragma unroll
         for (int e = 0; e < kBatch; ++e)
             if (e == nb) {
@@ -363,6 +371,7 @@ struct BrickSmem {
 // record, enters the segment at the piece's first step (one division per minor
 // axis) and steps through the piece with the carry recurrence, OR-ing bits into
 // the brick's shared bitmap; the bitmap is then merged into the volume.
+template <bool kEuclid>
 __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, const __grid_constant__ CUtensorMap tmap)
 {
     extern __shared__ __align__(128) unsigned char brick_smem_raw[];
@@ -431,11 +440,14 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
                 const int32_t len = static_cast<int32_t>(pc >> 54) + 1;
                 int32_t rec[6];
                 load_record(p.segs, static_cast<int64_t>(pc & 0xffffffffull), rec);
-                Stepper<uint32_t, uint32_t> st;
+                using St = typename std::conditional<kEuclid, EuclidStepper<uint32_t, uint32_t>,
+                                                     Stepper<uint32_t, uint32_t>>::type;
+                St st;
                 st.enter(rec, static_cast<int32_t>((pc >> 32) & 0x3fffffull), bw, bwh);
                 st.L -= origin;
                 // one shared-memory atomic per voxel: cheaper than branching to
-                // merge runs of the same word (measured on both workload shapes)
+                // merge runs of the same word (measured on both workload shapes);
+                // repeated samples of the Euclidean variant set the same bit again
                 int32_t e = 0;
                 for (; e + 4 <= len; e += 4) {
 #pragma unroll

@@ -263,4 +263,54 @@ __device__ __forceinline__ int32_t euclid_steps(const int32_t *rec)
     return isqrt_i64(s);
 }
 
+// Stepping state with the Euclidean N: no axis moves every step, so all three
+// carry (remainder r_a = (2 k A_a + N) mod 2N, the offset growing when it wraps).
+template <typename PackT, typename LinT>
+struct EuclidStepper {
+    int32_t twoN;
+    int32_t A2[3], r[3];
+    PackT P, dP[3];
+    LinT L, dL[3];
+
+    __device__ __forceinline__ void enter(const int32_t *rec, int32_t k, LinT w, LinT wh)
+    {
+        const int32_t N = euclid_steps(rec);
+        twoN = 2 * N;
+        int32_t v[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int32_t d = rec[3 + a] - rec[a];
+            const int32_t A = abs(d);
+            int32_t q = 0, rr = N;
+            if (k > 0) axis_entry(A, N, k, q, rr);
+            r[a] = rr;
+            A2[a] = 2 * A;
+            v[a] = rec[a] + (d >= 0 ? q : -q);
+            dP[a] = signed_step<PackT>(d, pack_unit<PackT>(a));
+            dL[a] = signed_step<LinT>(d, a == 0 ? LinT(1) : (a == 1 ? w : wh));
+        }
+        P = static_cast<PackT>(v[0]) | (static_cast<PackT>(v[1]) * pack_unit<PackT>(1)) |
+            (static_cast<PackT>(v[2]) * pack_unit<PackT>(2));
+        L = static_cast<LinT>(v[0]) + static_cast<LinT>(v[1]) * w + static_cast<LinT>(v[2]) * wh;
+    }
+
+    // Advance one sample; true when the voxel changed (some axis moved).
+    template <bool kP, bool kL>
+    __device__ __forceinline__ bool step()
+    {
+        bool moved = false;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            r[a] += A2[a];
+            if (r[a] >= twoN) {
+                r[a] -= twoN;
+                if (kP) P += dP[a];
+                if (kL) L += dL[a];
+                moved = true;
+            }
+        }
+        return moved;
+    }
+};
+
 }  // namespace vox

@@ -26,56 +26,6 @@ constexpr int64_t kEuclidMinRun = 32;       // samples per run at least
 constexpr int64_t kEuclidRunSlots = 1 << 20;  // run slots at least (more for many segments)
 
 
-// Stepping state with the Euclidean N: no axis moves every step, so all three
-// carry (remainder r_a = (2 k A_a + N) mod 2N, the offset growing when it wraps).
-template <typename PackT, typename LinT>
-struct EuclidStepper {
-    int32_t twoN;
-    int32_t A2[3], r[3];
-    PackT P, dP[3];
-    LinT L, dL[3];
-
-    __device__ __forceinline__ void enter(const int32_t *rec, int32_t k, LinT w, LinT wh)
-    {
-        const int32_t N = euclid_steps(rec);
-        twoN = 2 * N;
-        int32_t v[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const int32_t d = rec[3 + a] - rec[a];
-            const int32_t A = abs(d);
-            int32_t q = 0, rr = N;
-            if (k > 0) axis_entry(A, N, k, q, rr);
-            r[a] = rr;
-            A2[a] = 2 * A;
-            v[a] = rec[a] + (d >= 0 ? q : -q);
-            dP[a] = signed_step<PackT>(d, pack_unit<PackT>(a));
-            dL[a] = signed_step<LinT>(d, a == 0 ? LinT(1) : (a == 1 ? w : wh));
-        }
-        P = static_cast<PackT>(v[0]) | (static_cast<PackT>(v[1]) * pack_unit<PackT>(1)) |
-            (static_cast<PackT>(v[2]) * pack_unit<PackT>(2));
-        L = static_cast<LinT>(v[0]) + static_cast<LinT>(v[1]) * w + static_cast<LinT>(v[2]) * wh;
-    }
-
-    // Advance one sample; true when the voxel changed (some axis moved).
-    template <bool kP, bool kL>
-    __device__ __forceinline__ bool step()
-    {
-        bool moved = false;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            r[a] += A2[a];
-            if (r[a] >= twoN) {
-                r[a] -= twoN;
-                if (kP) P += dP[a];
-                if (kL) L += dL[a];
-                moved = true;
-            }
-        }
-        return moved;
-    }
-};
-
 struct EuclidParams {
     const int32_t *segs;
     int64_t n;
@@ -89,6 +39,8 @@ struct EuclidParams {
     uint32_t *mask;
     int64_t *seg_off;        // [n] first output position per segment, or null
     int32_t *status;
+    const int64_t *gate_total;  // if set (write pass), run only when *gate_total > gate_cap
+    int64_t gate_cap;
 };
 
 // One thread per run of consecutive samples (grid-stride over the run slots).
@@ -100,6 +52,7 @@ __global__ void __launch_bounds__(256) k_euclid_runs(EuclidParams p)
     constexpr bool kList = (OUT & (kOutList32 | kOutList64)) != 0;
     constexpr bool kMask = (OUT & kOutMask) != 0;
     if (ld_volatile_i32(p.status) != 0) return;  // an earlier error: write nothing
+    if (kWrite && p.gate_total != nullptr && __ldg(p.gate_total) <= p.gate_cap) return;  // the bricks took it
     const int64_t Vs = __ldg(p.offsets + p.n);
     const int64_t L = max(kEuclidMinRun, (Vs + p.n_runs - 1) / p.n_runs);
     if (kWrite && kList && __ldg(p.run_off + p.n_runs) > p.capacity) {
@@ -159,7 +112,7 @@ __global__ void __launch_bounds__(256) k_euclid_runs(EuclidParams p)
             add = st.template step<kWrite && kList, kWrite && kMask>();
             first = false;
         }
-        const int64_t base = kWrite ? __ldg(p.run_off + j) : 0;
+        const int64_t base = (kWrite && (kList || p.seg_off != nullptr)) ? __ldg(p.run_off + j) : 0;
         int32_t cnt = 0;
         LinT cur_word = static_cast<LinT>(~LinT(0));
         uint32_t acc = 0;
@@ -193,6 +146,119 @@ __global__ void __launch_bounds__(256) k_euclid_runs(EuclidParams p)
         }
         if (kWrite && kMask && acc) red_or_keep(p.mask + cur_word, acc, keep_policy);
         if (!kWrite) p.run_count[j] = cnt;
+    }
+}
+
+// The list writer: like the write pass of k_euclid_runs, but a warp takes 32
+// consecutive runs (one per lane) and walks them in lock step (every run has L
+// samples, the last ones fewer), each lane appending its voxels to its own row
+// of a shared-memory stage; whenever a row fills, the warp flushes every row,
+// row by row, with coalesced stores at the rows' list positions. Segment offsets
+// and (optionally) the volume's atomics are written on the way.
+constexpr int kEuclidRow = 16;  // stage entries per lane
+
+template <int OUT, bool LIN64>
+__global__ void __launch_bounds__(256) k_euclid_list(EuclidParams p)
+{
+    using PackT = typename std::conditional<(OUT & kOutList64) != 0, uint64_t, uint32_t>::type;
+    using LinT = typename std::conditional<LIN64, uint64_t, uint32_t>::type;
+    constexpr bool kMask = (OUT & kOutMask) != 0;
+    constexpr int kStride = kEuclidRow + 1;  // padded rows: lanes at equal fill hit different banks
+    __shared__ PackT stage[8][32 * kStride];
+    if (ld_volatile_i32(p.status) != 0) return;
+    if (__ldg(p.run_off + p.n_runs) > p.capacity) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(p.status, kStCapacity);
+        return;
+    }
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    PackT *const rows = stage[wib];
+    PackT *const row = rows + lane * kStride;
+    const int64_t Vs = __ldg(p.offsets + p.n);
+    const int64_t L = max(kEuclidMinRun, (Vs + p.n_runs - 1) / p.n_runs);
+    uint64_t keep_policy = 0;
+    if (kMask) asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep_policy));
+    const LinT w = static_cast<LinT>(p.w);
+    const LinT wh = static_cast<LinT>(p.w) * static_cast<LinT>(p.h);
+    PackT *const list = static_cast<PackT *>(p.list);
+    const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x / 32);
+    for (int64_t jw = (static_cast<int64_t>(blockIdx.x) * (blockDim.x / 32) + wib) * 32; jw < p.n_runs;
+         jw += warps * 32) {
+        const int64_t j = jw + lane;
+        const int64_t g0 = j * L;
+        const bool has = j < p.n_runs && g0 < Vs;
+        const int64_t g1 = has ? min(g0 + L, Vs) : g0;
+        int64_t s = 0, seg_end = 0, outp = 0;
+        int32_t rec[6] = {0, 0, 0, 0, 0, 0};
+        EuclidStepper<PackT, LinT> st;
+        bool add = false, first = false;
+        if (has) {
+            int64_t lo = 0, hi = p.n;
+            while (hi - lo > 1) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (__ldg(p.offsets + mid) <= g0) lo = mid;
+                else hi = mid;
+            }
+            s = lo;
+            seg_end = __ldg(p.offsets + s + 1);
+            load_record(p.segs, s, rec);
+            const int32_t k0 = static_cast<int32_t>(g0 - __ldg(p.offsets + s));
+            if (k0 == 0) {
+                st.enter(rec, 0, w, wh);
+                add = first = true;
+            } else {
+                st.enter(rec, k0 - 1, w, wh);
+                add = st.template step<true, kMask>();
+            }
+            outp = __ldg(p.run_off + j);
+        }
+        int f = 0;
+        LinT cur_word = static_cast<LinT>(~LinT(0));
+        uint32_t acc = 0;
+        auto flush = [&]() {
+#pragma unroll 1
+            for (int l = 0; l < 32; ++l) {
+                const int fl = __shfl_sync(0xffffffffu, f, l);
+                const int64_t ol = __shfl_sync(0xffffffffu, outp, l);
+                if (lane < fl) list[ol + lane] = rows[l * kStride + lane];
+            }
+            __syncwarp();
+            outp += f;
+            f = 0;
+        };
+#pragma unroll 1
+        for (int64_t it = 0; it < L; ++it) {
+            const int64_t g = g0 + it;
+            if (g < g1) {
+                if (g == seg_end) {  // the next segment starts here
+                    ++s;
+                    seg_end = __ldg(p.offsets + s + 1);
+                    load_record(p.segs, s, rec);
+                    st.enter(rec, 0, w, wh);
+                    add = first = true;
+                }
+                if (add) {
+                    if (first && p.seg_off != nullptr) p.seg_off[s] = outp + f;
+                    row[f++] = st.P;
+                    if constexpr (kMask) {
+                        const LinT word = st.L >> 5;
+                        if (word != cur_word) {
+                            if (acc) red_or_keep(p.mask + cur_word, acc, keep_policy);
+                            cur_word = word;
+                            acc = 0;
+                        }
+                        acc |= 1u << (static_cast<uint32_t>(st.L) & 31u);
+                    }
+                }
+                first = false;
+                if (g + 1 < seg_end) add = st.template step<true, kMask>();
+            }
+            __syncwarp();
+            if (__any_sync(0xffffffffu, f == kEuclidRow)) flush();
+        }
+        __syncwarp();
+        flush();
+        if (kMask && acc) red_or_keep(p.mask + cur_word, acc, keep_policy);
     }
 }
 

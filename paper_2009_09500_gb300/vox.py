@@ -42,7 +42,7 @@ EXPORTED = (
     "vox_workspace_size_volume", "vox_plan", "vox_workspace_size_batched", "vox_generate_batched",
     "vox_set_tuning", "vox_get_tuning", "vox_host_arena_size_volume",
     "vox_mask_words_bricked", "vox_brick_shape", "vox_unbrick",
-    "vox_euclid_workspace_size", "vox_euclid_generate", "vox_euclid_plan",
+    "vox_euclid_workspace_size", "vox_euclid_generate", "vox_euclid_plan", "vox_euclid_workspace_size_volume",
 )
 
 VOLUME_AUTO = 0
@@ -108,7 +108,9 @@ def load(path: str | None = None):
     lib.vox_euclid_workspace_size.restype = sz
     lib.vox_euclid_generate.argtypes = [vp, i64, Dims, vp, i64, vp, i32, vp, vp, sz, vp, vp]
     lib.vox_euclid_generate.restype = i32
-    lib.vox_euclid_plan.argtypes = [vp, i64, Dims, vp, sz, vp, vp, vp, vp]
+    lib.vox_euclid_plan.argtypes = [vp, i64, Dims, vp, sz, vp, vp, vp, vp, vp]
+    lib.vox_euclid_workspace_size_volume.argtypes = [i64, Dims, i64]
+    lib.vox_euclid_workspace_size_volume.restype = sz
     lib.vox_euclid_plan.restype = i32
     lib.vox_generate_host.argtypes = [vp, i64, Dims, vp, i64, vp, i32, vp, sz, vp, vp]
     lib.vox_generate_host.restype = i32
@@ -316,13 +318,20 @@ def vox_euclid_workspace_size(n: int) -> int:
     return int(load().vox_euclid_workspace_size(int(n)))
 
 
-def vox_euclid_plan(segs, dims, ws, status, stream=None):
-    """(total voxels, total samples) of the Euclidean-N variant (synchronous)."""
-    v, s = ctypes.c_int64(0), ctypes.c_int64(0)
+def vox_euclid_workspace_size_volume(n: int, dims, piece_capacity: int) -> int:
+    return int(load().vox_euclid_workspace_size_volume(int(n), _dims(dims), int(piece_capacity)))
+
+
+def vox_euclid_plan(segs, dims, ws, status, stream=None, with_pieces=False):
+    """(total voxels, total samples[, brick pieces]) of the Euclidean-N variant
+    (synchronous)."""
+    v, s, pc = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
     st = load().vox_euclid_plan(_ptr(segs), segs.shape[0], _dims(dims), _ptr(ws), ws.numel(), _ptr(status),
-                                ctypes.byref(v), ctypes.byref(s), _stream(stream))
+                                ctypes.byref(v), ctypes.byref(s), ctypes.byref(pc), _stream(stream))
     if st != OK:
         raise VoxError(st, "vox_euclid_plan")
+    if with_pieces:
+        return int(v.value), int(s.value), int(pc.value)
     return int(v.value), int(s.value)
 
 

@@ -23,12 +23,20 @@ def _lib():
     vox.load()
 
 
-def run_euclid(segs_np, dims, flags, capacity=None, mask_init=None, extra=64):
+def run_euclid(segs_np, dims, flags, capacity=None, mask_init=None, extra=64, pieces=None, offsets=True):
+    """pieces: None for the plain workspace (volume by atomics), "plan" for a
+    brick workspace sized by the plan, or an explicit piece capacity."""
     O = get_oracle()
     segs = torch.from_numpy(np.ascontiguousarray(segs_np, dtype=np.int32)).cuda()
     n = segs.shape[0]
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
-    ws = torch.empty(vox.vox_euclid_workspace_size(n), dtype=torch.uint8, device="cuda")
+    if pieces is None:
+        ws = torch.empty(vox.vox_euclid_workspace_size(n), dtype=torch.uint8, device="cuda")
+    else:
+        ws = torch.empty(vox.vox_euclid_workspace_size_volume(n, dims, 0), dtype=torch.uint8, device="cuda")
+        P = vox.vox_euclid_plan(segs, dims, ws, status, with_pieces=True)[2] if n else 0
+        cap_p = P if pieces == "plan" else int(pieces)
+        ws = torch.empty(vox.vox_euclid_workspace_size_volume(n, dims, cap_p), dtype=torch.uint8, device="cuda")
     Vd, Vs = vox.vox_euclid_plan(segs, dims, ws, status) if n else (0, 0)
     counts = O.euclid_count(segs_np) if n else np.zeros(0, np.int64)
     assert Vd == int(counts.sum())
@@ -42,10 +50,11 @@ def run_euclid(segs_np, dims, flags, capacity=None, mask_init=None, extra=64):
         words = vox.vox_mask_words(dims)
         mask = (torch.zeros(words, dtype=torch.int32, device="cuda") if mask_init is None
                 else torch.from_numpy(mask_init.view(np.int32).copy()).cuda())
-    offs = torch.full((n + 1,), -1, dtype=torch.int64, device="cuda")
+    offs = torch.full((n + 1,), -1, dtype=torch.int64, device="cuda") if offsets else None
     vox.vox_euclid_generate(segs, dims, ws, status, lst, mask, flags, offs, capacity=cap)
     torch.cuda.synchronize()
-    return {"status": int(status.item()), "Vd": Vd, "counts": counts, "offsets": offs.cpu().numpy(),
+    return {"status": int(status.item()), "Vd": Vd, "counts": counts,
+            "offsets": None if offs is None else offs.cpu().numpy(),
             "list": None if lst is None else lst.cpu().numpy(), "mask": None if mask is None else mask.cpu().numpy().view(np.uint32)}
 
 
@@ -54,7 +63,8 @@ def check(segs, dims, flags, **kw):
     r = run_euclid(segs, dims, flags, **kw)
     assert r["status"] == 0, vox.strerror(r["status"])
     Vd = r["Vd"]
-    assert np.array_equal(r["offsets"], np.concatenate([[0], np.cumsum(r["counts"])]))
+    if r["offsets"] is not None:
+        assert np.array_equal(r["offsets"], np.concatenate([[0], np.cumsum(r["counts"])]))
     if flags & (L32 | L64):
         want = O.euclid_list64(segs) if flags & L64 else O.euclid_list32(segs)
         got = r["list"][:Vd].view(want.dtype)
@@ -140,3 +150,39 @@ def test_fresh_volume_and_out_of_bounds():
 def test_empty_input():
     r = run_euclid(np.zeros((0, 6), np.int32), (8, 8, 8), L32)
     assert r["status"] == 0 and r["offsets"][0] == 0
+
+
+# ------------------------------------------------- the variant's volume by bricks
+@pytest.mark.parametrize("which,flags,pieces", [
+    ("config1", L32 | BM, "plan"), ("config1", BM, "plan"), ("config1", L64 | BM | FR, "plan"),
+    ("config1", L32 | BM, 100),       # pieces do not fit: atomics on the device
+    ("config1", BM | FR, 100),
+])
+def test_bricks_volume(which, flags, pieces):
+    w = getattr(workloads, which)()
+    rng = np.random.default_rng(12)
+    init = rng.integers(0, 2**32, size=vox.vox_mask_words(w.dims), dtype=np.uint64).astype(np.uint32)
+    check(w.segs, w.dims, flags, pieces=pieces, mask_init=init)
+
+
+@pytest.mark.parametrize("dims", [(96, 40, 17), (32, 7, 5), (128, 128, 64)])
+def test_bricks_volume_shapes(dims):
+    rng = np.random.default_rng(sum(dims))
+    check(workloads.uniform_segments(rng, 3000, dims), dims, L32 | BM, pieces="plan")
+
+
+def test_bricks_config2_full_size():
+    w = workloads.config2()
+    rng = np.random.default_rng(13)
+    init = rng.integers(0, 2**32, size=vox.vox_mask_words(w.dims), dtype=np.uint64).astype(np.uint32)
+    check(w.segs, w.dims, L32 | BM | FR, pieces="plan", mask_init=init)
+
+
+def test_bricks_volume_only_with_offsets_and_capacity_error():
+    w = workloads.config1()
+    check(w.segs, w.dims, BM, pieces="plan")  # offsets from a list-free write pass
+    O = get_oracle()
+    Vd = int(O.euclid_count(w.segs).sum())
+    r = run_euclid(w.segs, w.dims, L32 | BM, capacity=Vd - 1, pieces="plan")
+    assert r["status"] == vox.ERR_CAPACITY
+    assert (r["list"] == SENT).all() and (r["mask"] == 0).all()
