@@ -7,7 +7,7 @@ and caches it in a JSON file keyed by the GPU name and a workload class, so a
 later run with a similar workload reuses it without measuring.
 
 Tuned knobs (see include/vox.h, vox_tuning):
-  run_len      voxels per thread run in the generation kernel (16 or 32)
+  run_len      voxels per thread run in the generation kernel (16, 32 or 64)
   volume_path  bricks when the workspace allows (auto) or per-voxel atomics
   ctas_per_sm  persistent CTAs per SM (0 = occupancy maximum, or fewer)
 """
@@ -22,7 +22,7 @@ from . import vox
 
 CANDIDATES = [
     {"run_len": r, "volume_path": vp, "ctas_per_sm": c}
-    for r in (32, 16)
+    for r in (32, 64, 16)
     for vp in (vox.VOLUME_AUTO, vox.VOLUME_ATOMIC)
     for c in (0, 2)
 ]

@@ -378,6 +378,7 @@ vox_status launch_gen_t(const GenParams &p, cudaStream_t stream)
         return launch_gen_r<16, OUT, LIN64>(p, stream);
     } else {
         if (current_tuning().run_len == 16) return launch_gen_r<16, OUT, LIN64>(p, stream);
+        if (current_tuning().run_len == 64) return launch_gen_r<64, OUT, LIN64>(p, stream);
         return launch_gen_r<32, OUT, LIN64>(p, stream);
     }
 }
@@ -1185,7 +1186,7 @@ void vox_set_tuning(const vox_tuning *t)
         return;
     }
     g_tuning = *t;
-    if (g_tuning.run_len != 16 && g_tuning.run_len != 32) g_tuning.run_len = 0;
+    if (g_tuning.run_len != 16 && g_tuning.run_len != 32 && g_tuning.run_len != 64) g_tuning.run_len = 0;
     if (g_tuning.volume_path < 0 || g_tuning.volume_path > VOX_VOLUME_ATOMIC) g_tuning.volume_path = 0;
     if (g_tuning.ctas_per_sm < 0) g_tuning.ctas_per_sm = 0;
     g_tuning.reserved = 0;

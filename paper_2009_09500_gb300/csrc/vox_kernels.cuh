@@ -269,13 +269,15 @@ struct GenParams {
 
 // Shared memory of k_generate: the staged window of segments and, for list
 // outputs, the pass's voxels in a transposed layout (run slot u of thread t at
-// u * S + t, S = 256 + 32 / R) that is free of bank conflicts both when the
-// threads write their runs and when the pass is read back four voxels per thread.
+// u * S + t, S = 256 + 32 / R, or 257 for R >= 32) that is free of bank
+// conflicts when the threads write their runs and when the pass is read back
+// four voxels per thread (two-way for R = 64, where a warp reads 16 slots of
+// each of two threads).
 template <int R, int OUT>
 struct GenLayout {
     static constexpr bool kList = (OUT & (kOutList32 | kOutList64)) != 0;
     static constexpr bool kWide = (OUT & kOutList64) != 0;
-    static constexpr int S = kGenThreads + 32 / R;
+    static constexpr int S = kGenThreads + (R >= 32 ? 1 : 32 / R);
     static constexpr int kPlanes = kWide ? 2 : 1;
     static constexpr int kStageWords = kList ? kPlanes * R * S : 4;
 };

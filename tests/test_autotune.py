@@ -40,4 +40,4 @@ def test_tuning_set_get_and_sanitised():
 
 def test_candidates_cover_the_knobs():
     keys = {(c["run_len"], c["volume_path"], c["ctas_per_sm"]) for c in autotune.CANDIDATES}
-    assert {16, 32} == {k[0] for k in keys} and {0, 1} == {k[1] for k in keys} and len(keys) == 8
+    assert {16, 32, 64} == {k[0] for k in keys} and {0, 1} == {k[1] for k in keys} and len(keys) == 12
