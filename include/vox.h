@@ -145,6 +145,20 @@ vox_status vox_generate(const vox_segment *d_segs, int64_t n, vox_dims dims,
                         void *d_ws, size_t ws_bytes, int32_t *d_status, void *stream);
 
 /*
+ * vox_count_bins -- the brick binning's counting pass alone: pieces per brick
+ * slot, the part of vox_count that runs when ws_bytes covers the brick arrays
+ * (vox_workspace_size_volume). With vox_count given ws_bytes =
+ * vox_workspace_size(n) (count + scan only) the two passes can run on two
+ * streams: they read only the segments and write disjoint workspace parts. A
+ * volume generated after both then needs the full ws_bytes and a stream ordered
+ * after both. Asynchronous; does not touch the status word (segments with
+ * endpoints outside the volume are skipped; vox_count reports them).
+ * VOX_ERR_WORKSPACE when the workspace does not hold the brick arrays.
+ */
+vox_status vox_count_bins(const vox_segment *d_segs, int64_t n, vox_dims dims, void *d_ws, size_t ws_bytes,
+                          void *stream);
+
+/*
  * vox_generate_from_scan -- the generation step alone, reusing the counts and
  * offsets that a preceding vox_count left in d_ws for the same d_segs, n and
  * dims, on the same stream (or on a stream ordered after it). Does not reset

@@ -171,10 +171,12 @@ class PlainScenes:
 
 class SceneStep:
     """One scene's whole step -- count + scan, the list, a fresh volume -- on
-    resident device buffers, captured once as a CUDA graph. After the count the
-    list and the volume are issued on two streams: the two calls share only
-    read-only parts of the workspace (the segments and the scanned offsets), so
-    the list kernel and the volume's binning overlap on the device.
+    resident device buffers, captured once as a CUDA graph, on two streams: the
+    brick binning's counting pass (vox_count_bins) runs beside the count + scan
+    (they read only the segments and write disjoint workspace parts), then the
+    list follows the scan on one stream and the volume follows both on the other
+    (the two calls share only read-only workspace parts), so the list kernel and
+    the volume's binning overlap on the device.
 
     segs: int32 [n, 6] on the device; list_flag: vox.OUT_LIST32, vox.OUT_LIST64
     or 0 (no list); volume: build the occupancy volume too."""
@@ -196,32 +198,43 @@ class SceneStep:
             dt = torch.int64 if self.list_flag == vox.OUT_LIST64 else torch.int32
             self.lst = torch.empty(max(self.V, 1), dtype=dt, device=device)
         self.mask = torch.empty(vox.vox_mask_words(self.dims), dtype=torch.int32, device=device) if volume else None
+        self.plain_ws_bytes = vox.vox_workspace_size(n)  # count + scan only
+        self.bricks = bool(volume and n and self.P > 0)
         self.side = torch.cuda.Stream(device=device)
         self.graph = GraphRunner(self.launch)
 
     def launch(self, s):
-        """Enqueue the step on stream `s` (the list on a second stream, joined back)."""
+        """Enqueue the step on stream `s` (the volume on a second stream, joined back)."""
         import torch
 
-        vox.vox_count(self.segs, self.dims, self.ws, self.status, None, None, s)
-        if self.segs.shape[0] == 0:
+        if self.segs.shape[0] == 0 or not self.volume:
+            vox.vox_count(self.segs, self.dims, self.ws, self.status, None, None, s)
             if self.volume:
                 vox.vox_generate_from_scan(self.segs, self.dims, self.ws, self.status, None, self.mask,
                                            vox.OUT_BITMASK | vox.OUT_FRESH, s)
+            if self.list_flag and self.segs.shape[0]:
+                vox.vox_generate_from_scan(self.segs, self.dims, self.ws, self.status, self.lst, None, self.list_flag,
+                                           s, capacity=self.V)
             return
+        start = torch.cuda.Event()
+        start.record(s)
+        self.side.wait_event(start)
+        if self.bricks:  # the binning's count beside the count + scan
+            vox.vox_count_bins(self.segs, self.dims, self.ws, self.side)
+            vox.vox_count(self.segs, self.dims, self.ws, self.status, None, None, s, ws_bytes=self.plain_ws_bytes)
+        else:
+            vox.vox_count(self.segs, self.dims, self.ws, self.status, None, None, s)
         counted = torch.cuda.Event()
         counted.record(s)
+        self.side.wait_event(counted)  # a count error keeps the volume from being written
+        vox.vox_generate_from_scan(self.segs, self.dims, self.ws, self.status, None, self.mask,
+                                   vox.OUT_BITMASK | vox.OUT_FRESH, self.side)
         if self.list_flag:
-            self.side.wait_event(counted)
-            vox.vox_generate_from_scan(self.segs, self.dims, self.ws, self.status, self.lst, None, self.list_flag,
-                                       self.side, capacity=self.V)
-        if self.volume:
-            vox.vox_generate_from_scan(self.segs, self.dims, self.ws, self.status, None, self.mask,
-                                       vox.OUT_BITMASK | vox.OUT_FRESH, s)
-        if self.list_flag:
-            listed = torch.cuda.Event()
-            listed.record(self.side)
-            s.wait_event(listed)
+            vox.vox_generate_from_scan(self.segs, self.dims, self.ws, self.status, self.lst, None, self.list_flag, s,
+                                       capacity=self.V)
+        done = torch.cuda.Event()
+        done.record(self.side)
+        s.wait_event(done)
 
     def replay(self):
         """Replay the captured step on the current stream (asynchronous)."""

@@ -799,6 +799,29 @@ vox_status vox_count(const vox_segment *d_segs, int64_t n, vox_dims dims, int32_
     return launch_count_scan(d_segs, n, dims, d_counts, d_offsets, d_ws, ws_bytes, d_status, s);
 }
 
+vox_status vox_count_bins(const vox_segment *d_segs, int64_t n, vox_dims dims, void *d_ws, size_t ws_bytes,
+                          void *stream)
+{
+    if (n < 0 || (n > 0 && d_segs == nullptr)) return VOX_ERR_INVALID_ARG;
+    if (vox_status e = check_dims(dims)) return e;
+    if (n > 0 && !aligned(d_segs, 16)) return VOX_ERR_ALIGNMENT;
+    if (d_ws == nullptr || !aligned(d_ws, kWsAlign)) return VOX_ERR_WORKSPACE;
+    if (n == 0) return VOX_OK;
+    BrickGeom G;
+    if (!uses_bricks(n, dims, ws_bytes, &G)) return VOX_ERR_WORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const VolLayout VL = vol_layout(n, G, 0);
+    char *base = static_cast<char *>(d_ws);
+    if (cudaMemsetAsync(base + VL.hdr, 0, VL.off - VL.hdr, s) != cudaSuccess) return VOX_ERR_CUDA;
+    BinParams bp{};
+    bp.segs = reinterpret_cast<const int32_t *>(d_segs);
+    bp.n = n;
+    bp.G = G;
+    bp.brick_count = reinterpret_cast<int32_t *>(base + VL.count);
+    k_bin_count<false><<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(bp);
+    return cudaGetLastError() == cudaSuccess ? VOX_OK : VOX_ERR_CUDA;
+}
+
 vox_status vox_generate(const vox_segment *d_segs, int64_t n, vox_dims dims, void *d_list, int64_t list_capacity,
                         uint32_t *d_mask, int flags, void *d_ws, size_t ws_bytes, int32_t *d_status, void *stream)
 {

@@ -212,11 +212,14 @@ __device__ __forceinline__ void load_record(const int32_t *segs, int64_t s, int3
 template <bool kEuclid>
 __global__ void __launch_bounds__(256) k_bin_count(BinParams p)
 {
+    // no status check: this pass may run beside the count + scan that resets the
+    // status word; it only writes the slot counts, and segments with endpoints
+    // outside the volume (reported by the count kernel) are skipped
     const int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (s >= p.n || ld_volatile_i32(p.status) != 0) return;
+    if (s >= p.n) return;
     int32_t r[6];
     load_record(p.segs, s, r);
-    if (!endpoints_inside(r, p.G)) return;  // reported by the count kernel
+    if (!endpoints_inside(r, p.G)) return;
     const int32_t rep = static_cast<int32_t>(s) & (p.G.reps - 1);
     for_each_piece<kEuclid>(r, p.G, [&](int32_t b, int32_t, int32_t len) {
         atomicAdd(p.brick_count + piece_slot(p.G, b, len, rep), 1);

@@ -43,6 +43,7 @@ EXPORTED = (
     "vox_set_tuning", "vox_get_tuning", "vox_host_arena_size_volume",
     "vox_mask_words_bricked", "vox_brick_shape", "vox_unbrick",
     "vox_euclid_workspace_size", "vox_euclid_generate", "vox_euclid_plan", "vox_euclid_workspace_size_volume",
+    "vox_count_bins",
 )
 
 VOLUME_AUTO = 0
@@ -90,6 +91,8 @@ def load(path: str | None = None):
     lib.vox_workspace_size.restype = sz
     lib.vox_count.argtypes = [vp, i64, Dims, vp, vp, vp, sz, vp, vp]
     lib.vox_count.restype = i32
+    lib.vox_count_bins.argtypes = [vp, i64, Dims, vp, sz, vp]
+    lib.vox_count_bins.restype = i32
     for name in ("vox_generate", "vox_generate_from_scan"):
         f = getattr(lib, name)
         f.argtypes = [vp, i64, Dims, vp, i64, vp, i32, vp, sz, vp, vp]
@@ -232,13 +235,23 @@ def _check_segs(segs):
         raise ValueError("segments must be a contiguous CUDA int32 tensor of shape [n, 6]")
 
 
-def vox_count(segs, dims, ws, status, counts=None, offsets=None, stream=None) -> None:
+def vox_count(segs, dims, ws, status, counts=None, offsets=None, stream=None, ws_bytes=None) -> None:
     """Launch the count + scan on ``stream``; raises on host-side errors only
-    (device errors land in ``status``)."""
+    (device errors land in ``status``). ``ws_bytes`` (default: all of ``ws``) set
+    to vox_workspace_size(n) leaves the brick binning's count to vox_count_bins."""
     _check_segs(segs)
+    nbytes = ws.numel() * ws.element_size() if ws_bytes is None else int(ws_bytes)
     st = load().vox_count(_ptr(segs), segs.shape[0], _dims(dims), _ptr(counts), _ptr(offsets),
-                          _ptr(ws), ws.numel() * ws.element_size(), _ptr(status), _stream(stream))
+                          _ptr(ws), nbytes, _ptr(status), _stream(stream))
     _check(st, "vox_count")
+
+
+def vox_count_bins(segs, dims, ws, stream=None) -> None:
+    """The brick binning's counting pass alone (asynchronous)."""
+    _check_segs(segs)
+    st = load().vox_count_bins(_ptr(segs), segs.shape[0], _dims(dims), _ptr(ws), ws.numel() * ws.element_size(),
+                               _stream(stream))
+    _check(st, "vox_count_bins")
 
 
 def _gen(fn, segs, dims, ws, status, list_out=None, mask=None, flags=None, stream=None, capacity=None):

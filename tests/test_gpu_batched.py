@@ -195,3 +195,30 @@ def test_scene_step_list64_only_and_empty():
     empty.replay()
     torch.cuda.synchronize()
     assert int(empty.status.item()) == 0 and bool((empty.mask == 0).all())
+
+
+def test_count_bins_beside_the_scan():
+    """vox_count on the count + scan part of the workspace and vox_count_bins on
+    a second stream, then the volume: the oracle's volume; a workspace without
+    the brick arrays is refused."""
+    O = get_oracle()
+    w = workloads.config1()
+    segs = torch.from_numpy(w.segs).cuda()
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ws = torch.empty(vox.vox_workspace_size_volume(w.n, w.dims, 0), dtype=torch.uint8, device="cuda")
+    V, P = vox.vox_plan(segs, w.dims, ws, st)
+    ws = torch.empty(vox.vox_workspace_size_volume(w.n, w.dims, P), dtype=torch.uint8, device="cuda")
+    mask = torch.full((vox.vox_mask_words(w.dims),), -1, dtype=torch.int32, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    vox.vox_count_bins(segs, w.dims, ws, side)
+    vox.vox_count(segs, w.dims, ws, st, ws_bytes=vox.vox_workspace_size(w.n))
+    torch.cuda.current_stream().wait_stream(side)
+    vox.vox_generate_from_scan(segs, w.dims, ws, st, None, mask, vox.OUT_BITMASK | vox.OUT_FRESH)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    assert np.array_equal(mask.cpu().numpy().view(np.uint32), O.bitmask(w.segs, w.dims))
+    small = torch.empty(vox.vox_workspace_size(w.n), dtype=torch.uint8, device="cuda")
+    with pytest.raises(vox.VoxError) as e:
+        vox.vox_count_bins(segs, w.dims, small)
+    assert e.value.status == vox.ERR_WORKSPACE
