@@ -433,7 +433,11 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     flags = vox.OUT_LIST32 | vox.OUT_BITMASK | vox.OUT_FRESH
     tuning = None
-    if not args.no_tune:  # launch tuning for this GPU and workload class (outputs do not depend on it)
+    if args.tuning:  # a given launch tuning (e.g. the one the tuner picks, for a profiler run)
+        r, vp, c = (int(x) for x in args.tuning.split(","))
+        vox.vox_set_tuning(r, vp, c)
+        tuning = {"params": {"run_len": r, "volume_path": vp, "ctas_per_sm": c}, "given": True}
+    elif not args.no_tune:  # launch tuning for this GPU and workload class (outputs do not depend on it)
         from paper_2009_09500_gb300 import autotune
 
         tuning = autotune.get_or_tune(lambda: vox.vox_generate(segs, w.dims, ws, status, lst, mask, flags),
@@ -539,7 +543,7 @@ def run_ours(args):
     # the brick-major volume layout (VOX_OUT_BRICKED): the same volume phase with one
     # contiguous bulk copy per brick, and the conversion back to row-major
     bricked = None
-    if vox.vox_mask_words_bricked(w.dims) > 0:
+    if not args.no_bricked and vox.vox_mask_words_bricked(w.dims) > 0:
         bmask = torch.empty(vox.vox_mask_words_bricked(w.dims), dtype=torch.int32, device=dev)
         tb, tu = [], []
         for i in range(min(args.steps, 20) + 3):
@@ -690,6 +694,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-sweeps", action="store_true")
     ap.add_argument("--no-euclid", action="store_true")
+    ap.add_argument("--no-bricked", action="store_true")
+    ap.add_argument("--tuning", default="", help="run_len,volume_path,ctas_per_sm: use this launch tuning")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
