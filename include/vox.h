@@ -376,7 +376,7 @@ vox_status vox_generate_noalloc(const vox_segment *d_segs, int64_t n, vox_dims d
  * Launch tuning (process-wide, every device). The outputs do not depend on it:
  * only how the work is spread. Chosen by measurement (the Python autotuner).
  *   run_len       voxels per thread run in the list/atomic generation kernel:
- *                 16, 32 or 64 (0 = default: 32; 64-bit lists always use 16);
+ *                 16, 32 or 64 (0 = default: 32; 64-bit lists take 64 as 32);
  *                 longer runs pay the run's entry less often, shorter runs keep
  *                 more threads busy on small inputs
  *   volume_path   VOX_VOLUME_AUTO (bricks when the workspace allows) or

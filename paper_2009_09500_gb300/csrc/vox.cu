@@ -372,10 +372,11 @@ vox_status launch_gen_r(const GenParams &p, cudaStream_t stream)
 template <int OUT, bool LIN64>
 vox_status launch_gen_t(const GenParams &p, cudaStream_t stream)
 {
-    // run length: 32 voxels per thread by default, 16 when the 64-bit list
-    // doubles the staging; the tuning may ask for 16 with 32-bit outputs
+    // run length: 32 voxels per thread by default; the tuning may ask for 16 or
+    // 64 (64-bit lists, whose staging is twice as large, stop at 32)
     if constexpr ((OUT & kOutList64) != 0) {
-        return launch_gen_r<16, OUT, LIN64>(p, stream);
+        if (current_tuning().run_len == 16) return launch_gen_r<16, OUT, LIN64>(p, stream);
+        return launch_gen_r<32, OUT, LIN64>(p, stream);
     } else {
         if (current_tuning().run_len == 16) return launch_gen_r<16, OUT, LIN64>(p, stream);
         if (current_tuning().run_len == 64) return launch_gen_r<64, OUT, LIN64>(p, stream);

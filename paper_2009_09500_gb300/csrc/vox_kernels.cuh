@@ -35,7 +35,7 @@ constexpr uint64_t kDescInc = 2ull << 62;  // tile inclusive prefix published
 constexpr uint64_t kDescValue = (1ull << 62) - 1;
 
 constexpr int kGenThreads = 256;
-constexpr int kWindowSegs = 512;   // segment records staged per window (even)
+constexpr int kWindowSegs = 256;   // segment records staged per window (even)
 
 // Status codes written by the kernels (same values as the public vox_status).
 constexpr int32_t kStOutOfBounds = 2;
