@@ -65,9 +65,9 @@ def _kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def _recorded_traffic(kernels):
-    """DRAM bytes per launch (summed over `kernels`, one launch each) from the
-    committed ncu record, if every entry was taken on the current kernel sources
+def _recorded_field(kernels, field):
+    """Sum of `field` over `kernels` in the committed ncu record, if every entry
+    was taken on the current kernel sources with the launch tuning now in force
     (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
@@ -75,13 +75,37 @@ def _recorded_traffic(kernels):
             rec = json.load(f)
     except (OSError, ValueError):
         return None
+    from paper_2009_09500_gb300 import vox
+
+    now = vox.vox_get_tuning()
     total = 0.0
     for k in kernels:
         ent = rec.get(k)
-        if not ent or ent.get("source_hash") != _kernel_source_hash():
+        if not ent or ent.get("source_hash") != _kernel_source_hash() or field not in ent:
             return None
-        total += float(ent.get("dram_bytes_per_launch"))
+        if ent.get("tuning") is not None and ent["tuning"] != now:
+            return None
+        total += float(ent[field])
     return total
+
+
+def _issue(kernels, ms: float, sm_mhz: float, sms: int) -> dict | None:
+    """Issue-rate view of a phase: warp instructions the kernels executed (ncu
+    record, per launch) per second against the issue peak of 4 warp
+    instructions per SM per clock at the sampled SM clock."""
+    inst = _recorded_field(kernels, "warp_instructions")
+    if inst is None or not ms or not sm_mhz:
+        return None
+    peak = 4.0 * sms * sm_mhz * 1e6
+    achieved = inst / (ms * 1e-3)
+    return {"warp_instructions_per_launch": inst, "achieved_per_s": achieved, "peak_per_s": peak,
+            "frac": achieved / peak, "peak_model": f"4 warp instructions/clk/SM x {sms} SMs x {sm_mhz:.0f} MHz"}
+
+
+def _recorded_traffic(kernels):
+    """DRAM bytes per launch (summed over `kernels`, one launch each) from the
+    committed ncu record (see _recorded_field)."""
+    return _recorded_field(kernels, "dram_bytes_per_launch")
 
 
 def _link_bandwidth(dev, h_buf) -> dict:
@@ -533,7 +557,7 @@ def run_ours(args):
     vol_bytes = 24 * n + 4 * words
     roof_list = {"bound": "hbm", "achieved": list_bytes / list_mean / 1e6, "peak": hbm, "unit": "GB/s",
                  "frac": list_bytes / list_mean / 1e6 / hbm, "traffic": _recorded_traffic(["k_generate<list32>"]),
-                 "kernel": "k_generate<32, list32> (one launch)", "peak_kind": f"{peak_kind} HBM copy",
+                 "kernel": "k_generate<R, list32> (one launch; R from the tuning)", "peak_kind": f"{peak_kind} HBM copy",
                  "algorithmic_bytes_per_launch": list_bytes, "ms": list_mean,
                  "bytes_model": "24 B/segment read + 4 B/voxel written"}
     roof_vol = {"bound": "hbm", "achieved": vol_bytes / vol_mean / 1e6, "peak": hbm, "unit": "GB/s",
@@ -547,6 +571,11 @@ def run_ours(args):
                 "peak_kind": f"{peak_kind} HBM copy", "algorithmic_bytes_per_launch": vol_bytes, "ms": vol_mean,
                 "bytes_model": "24 B/segment read + the whole volume written once (w*h*d/8 bytes)",
                 "pieces": P}
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = (clocks or {}).get("sm_mhz") or (clocks or {}).get("sm_max_mhz")
+    roof_list["issue"] = _issue(["k_generate<list32>"], list_mean, mhz, sms)
+    roof_vol["issue"] = _issue(["k_scan<false>", "k_bin_scatter", "k_brick_volume", "k_generate<volume, gated>"],
+                               vol_mean, mhz, sms)
     roofline, roofline_other = (roof_vol, roof_list) if vol_mean >= list_mean else (roof_list, roof_vol)
 
     # the brick-major volume layout (VOX_OUT_BRICKED): the same volume phase with one
