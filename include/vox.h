@@ -221,11 +221,15 @@ vox_status vox_euclid_plan(const vox_segment *d_segs, int64_t n, vox_dims dims, 
  *   vox_brick_shape         h_shape[0..5] = B0, B1, B2, nb0, nb1, nb2 (host
  *                           int32[6]); VOX_ERR_INVALID_ARG when w % 32 != 0
  *   vox_unbrick             device brick-major volume -> device row-major volume
- *                           (vox_mask_words(dims) words), asynchronous on stream
+ *                           (vox_mask_words(dims) words), asynchronous on stream;
+ *                           half bricks through TMA when w and B0 are multiples of
+ *                           128 and both buffers 16-byte aligned (its bounded
+ *                           waits report VOX_ERR_TIMEOUT to d_status, which may be
+ *                           NULL), else one warp per volume row
  */
 int64_t vox_mask_words_bricked(vox_dims dims);
 vox_status vox_brick_shape(vox_dims dims, int32_t *h_shape);
-vox_status vox_unbrick(const uint32_t *d_bricked, vox_dims dims, uint32_t *d_mask, void *stream);
+vox_status vox_unbrick(const uint32_t *d_bricked, vox_dims dims, uint32_t *d_mask, int32_t *d_status, void *stream);
 
 /*
  * The occupancy volume can be built two ways; vox_generate picks one from the

@@ -202,7 +202,7 @@ bool make_geom(vox_dims dims, BrickGeom *G)
 // Tensor map of the volume as a 3-D array of 32-bit words (row_words x h x d)
 // with brick-sized boxes, for the TMA reduce-OR merge. Needs 16-byte aligned
 // rows and box rows (w and B0 multiples of 128) and a 16-byte aligned volume.
-bool make_volume_tmap(const BrickGeom &G, uint32_t *mask, CUtensorMap *out)
+bool make_volume_tmap(const BrickGeom &G, uint32_t *mask, CUtensorMap *out, int32_t box_z = 0)
 {
     if (G.bxw % 4 != 0 || G.row_words % 4 != 0 || !aligned(mask, 16)) return false;
     static std::mutex mu;
@@ -223,7 +223,7 @@ bool make_volume_tmap(const BrickGeom &G, uint32_t *mask, CUtensorMap *out)
                                 static_cast<cuuint64_t>(G.dim[2])};
     const cuuint64_t strides[2] = {4ull * G.row_words, 4ull * G.row_words * static_cast<cuuint64_t>(G.dim[1])};
     const cuuint32_t box[3] = {static_cast<cuuint32_t>(G.bxw), static_cast<cuuint32_t>(G.B[1]),
-                               static_cast<cuuint32_t>(G.B[2])};
+                               static_cast<cuuint32_t>(box_z > 0 ? box_z : G.B[2])};
     const cuuint32_t estr[3] = {1, 1, 1};
     if (box[1] > 256 || box[2] > 256) return false;
     return encode(out, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, mask, dims, strides, box, estr,
@@ -286,9 +286,11 @@ VolLayout vol_layout(int64_t n, const BrickGeom &G, int64_t capacity, size_t bas
 
 // Whether a call on n segments with this workspace builds the volume by brick
 // ownership (the workspace holds the brick arrays and room for a piece).
+// Pieces name their segment in 32 bits: beyond 2^32 segments the volume takes
+// the atomics path.
 bool uses_bricks(int64_t n, vox_dims dims, size_t ws_bytes, BrickGeom *G, size_t base = 0)
 {
-    return n > 0 && make_geom(dims, G) && ws_bytes >= vol_layout(n, *G, 1, base).total;
+    return n > 0 && n < (int64_t(1) << 32) && make_geom(dims, G) && ws_bytes >= vol_layout(n, *G, 1, base).total;
 }
 
 // Count + scan. With a brick workspace it also zeroes the brick arrays and
@@ -930,13 +932,27 @@ vox_status vox_brick_shape(vox_dims dims, int32_t *h_shape)
     return VOX_OK;
 }
 
-vox_status vox_unbrick(const uint32_t *d_bricked, vox_dims dims, uint32_t *d_mask, void *stream)
+vox_status vox_unbrick(const uint32_t *d_bricked, vox_dims dims, uint32_t *d_mask, int32_t *d_status, void *stream)
 {
     BrickGeom G;
     if (d_bricked == nullptr || d_mask == nullptr || !make_geom(dims, &G)) return VOX_ERR_INVALID_ARG;
     if (!aligned(d_bricked, 4) || !aligned(d_mask, 4)) return VOX_ERR_ALIGNMENT;
     const int sms = sm_count();
     if (sms <= 0) return VOX_ERR_CUDA;
+    // half bricks through the bulk-copy unit when the volume takes brick-shaped
+    // TMA boxes (w and B0 multiples of 128, 16-byte aligned buffers)
+    CUtensorMap tmap;
+    std::memset(&tmap, 0, sizeof(tmap));
+    if (G.B[2] % kUnbrickSplit == 0 && aligned(d_bricked, 16) &&
+        make_volume_tmap(G, d_mask, &tmap, G.B[2] / kUnbrickSplit)) {
+        const size_t smem = 4 * static_cast<size_t>(G.words / kUnbrickSplit);
+        if (vox_status e = allow_smem(reinterpret_cast<const void *>(k_unbrick_tma), smem)) return e;
+        const int grid = grid_ctas(reinterpret_cast<const void *>(k_unbrick_tma), 32, smem);
+        if (grid <= 0) return VOX_ERR_CUDA;
+        k_unbrick_tma<<<static_cast<unsigned>(grid), 32, smem, static_cast<cudaStream_t>(stream)>>>(
+            d_bricked, G, tmap, d_status, static_cast<uint64_t>(g_wait_ns.load()));
+        return cudaGetLastError() == cudaSuccess ? VOX_OK : VOX_ERR_CUDA;
+    }
     const int64_t rows = static_cast<int64_t>(dims.h) * dims.d;
     const int64_t blocks = std::min<int64_t>((rows + 7) / 8, static_cast<int64_t>(sms) * 16);
     k_unbrick<<<static_cast<unsigned>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(d_bricked, G, d_mask);

@@ -507,4 +507,50 @@ __global__ void __launch_bounds__(256) k_unbrick(const uint32_t *bricked, BrickG
     }
 }
 
+// Brick-major -> row-major through the bulk-copy unit: each CTA (one warp, of
+// which thread 0 works) takes half bricks in a grid-stride order; a half brick
+// is contiguous in the brick-major layout (z is the slowest axis inside a
+// brick), so it arrives in shared memory with one 1-D bulk copy and leaves with
+// one TMA tensor store of a half-brick box. Several CTAs per SM keep loads and
+// stores in flight together. Every wait is bounded; on expiry the status (if
+// any) records a timeout and the CTA stops after one more bounded wait for its
+// copy in flight.
+constexpr int kUnbrickSplit = 2;
+
+__global__ void __launch_bounds__(32) k_unbrick_tma(const uint32_t *bricked, BrickGeom G,
+                                                    const __grid_constant__ CUtensorMap tmap, int32_t *status,
+                                                    uint64_t wait_ns)
+{
+    extern __shared__ __align__(128) unsigned char unbrick_smem_raw[];
+    uint32_t *buf = reinterpret_cast<uint32_t *>(unbrick_smem_raw);
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    const int32_t part_words = G.words / kUnbrickSplit;
+    const int32_t part_rows = G.B[2] / kUnbrickSplit;
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+    uint32_t phase = 0;
+    const int64_t n_parts = G.n_bricks * kUnbrickSplit;
+    for (int64_t q = blockIdx.x; q < n_parts; q += gridDim.x) {
+        const int64_t b = q / kUnbrickSplit;
+        const int32_t h = static_cast<int32_t>(q - b * kUnbrickSplit);
+        const int64_t rest = b / G.nb[0];
+        const int32_t X0 = static_cast<int32_t>(b - rest * G.nb[0]) * G.B[0];
+        const int32_t Y0 = static_cast<int32_t>(rest % G.nb[1]) * G.B[1];
+        const int32_t Z0 = static_cast<int32_t>(rest / G.nb[1]) * G.B[2];
+        bulk_wait_read_all();  // the previous store has read the buffer
+        mbar_arrive_expect_tx(&bar, static_cast<uint32_t>(part_words) * 4u);
+        bulk_copy_g2s(buf, bricked + b * G.words + static_cast<int64_t>(h) * part_words,
+                      static_cast<uint32_t>(part_words) * 4u, &bar);
+        if (!mbar_wait_bounded(&bar, phase, wait_ns)) {
+            if (status != nullptr) set_status(status, 5);  // VOX_ERR_TIMEOUT
+            mbar_wait_bounded(&bar, phase, wait_ns);
+            break;
+        }
+        phase ^= 1u;
+        tma_store_3d(&tmap, buf, X0 / 32, Y0, Z0 + h * part_rows);
+    }
+    bulk_wait_all();
+}
+
 }  // namespace vox

@@ -105,7 +105,7 @@ def load(path: str | None = None):
     lib.vox_mask_words_bricked.restype = i64
     lib.vox_brick_shape.argtypes = [Dims, vp]
     lib.vox_brick_shape.restype = i32
-    lib.vox_unbrick.argtypes = [vp, Dims, vp, vp]
+    lib.vox_unbrick.argtypes = [vp, Dims, vp, vp, vp]
     lib.vox_unbrick.restype = i32
     lib.vox_euclid_workspace_size.argtypes = [i64]
     lib.vox_euclid_workspace_size.restype = sz
@@ -320,9 +320,9 @@ def vox_brick_shape(dims):
     return tuple(out[:3]), tuple(out[3:])
 
 
-def vox_unbrick(bricked, dims, mask, stream=None):
+def vox_unbrick(bricked, dims, mask, stream=None, status=None):
     """Brick-major volume (device int32 tensor) -> row-major volume `mask`."""
-    st = load().vox_unbrick(_ptr(bricked), _dims(dims), _ptr(mask), _stream(stream))
+    st = load().vox_unbrick(_ptr(bricked), _dims(dims), _ptr(mask), _ptr(status), _stream(stream))
     if st != OK:
         raise VoxError(st, "vox_unbrick")
 
