@@ -313,6 +313,35 @@ vox_status vox_generate_batched(const vox_segment *d_segs, int64_t n_total, cons
                                 void *stream);
 
 /*
+ * Batched volumes by bricks (the brick path of the single-scene volume, over
+ * all scenes at once; one counter replica, bricks merged by plain stores):
+ *   vox_scene_bricks   bricks of one scene's volume (its width a multiple of
+ *                      32), 0 when it cannot take bricks; host-only
+ *   vox_workspace_size_batched_volume  the batched workspace followed by the
+ *                      brick arrays of total_bricks bricks and piece_capacity
+ *                      pieces (vox_plan_batched gives the count)
+ *   vox_generate_batched_ex  vox_generate_batched with total_bricks = the sum of
+ *                      vox_scene_bricks over the scenes (every scene must take
+ *                      bricks; a different sum on the device is
+ *                      VOX_ERR_INVALID_ARG): with such a workspace the volumes
+ *                      are built by bricks, pieces beyond the capacity by the
+ *                      batched atomics on the device; total_bricks = 0 or a
+ *                      smaller workspace gives vox_generate_batched exactly
+ *   vox_plan_batched   SYNCHRONOUS: total voxels and brick pieces of a batch
+ *                      (pieces 0 when total_bricks is 0)
+ */
+int64_t vox_scene_bricks(vox_dims dims);
+size_t vox_workspace_size_batched_volume(int64_t n_total, int32_t n_scenes, int64_t total_bricks,
+                                         int64_t piece_capacity);
+vox_status vox_generate_batched_ex(const vox_segment *d_segs, int64_t n_total, const vox_scene *d_scenes,
+                                   int32_t n_scenes, int64_t total_bricks, void *d_list, int64_t list_capacity,
+                                   int flags, int64_t *d_scene_base, void *d_ws, size_t ws_bytes, int32_t *d_status,
+                                   void *stream);
+vox_status vox_plan_batched(const vox_segment *d_segs, int64_t n_total, const vox_scene *d_scenes, int32_t n_scenes,
+                            int64_t total_bricks, void *d_ws, size_t ws_bytes, int32_t *d_status, int64_t *h_voxels,
+                            int64_t *h_pieces, void *stream);
+
+/*
  * vox_generate_host -- vox_generate on host buffers, copies included (the
  * host-device pipeline of Fig. 4: input copy, kernels, result copy back).
  * SYNCHRONOUS: returns once the results are in host memory (it synchronises

@@ -62,16 +62,18 @@ class Batch:
     status: object
     flags: int
     V: int
+    total_bricks: int = 0  # > 0: the volumes by bricks (workspace sized for them)
+    pieces: int = 0
 
     def run(self, stream=None):
         """Enqueue the batched launch sequence on `stream` (asynchronous)."""
-        st = vox.load().vox_generate_batched(
-            vox._ptr(self.segs), self.segs.shape[0], vox._ptr(self.scenes), self.n_scenes,
+        st = vox.load().vox_generate_batched_ex(
+            vox._ptr(self.segs), self.segs.shape[0], vox._ptr(self.scenes), self.n_scenes, self.total_bricks,
             vox._ptr(self.lst), self.lst.numel() if self.lst is not None else 0, self.flags,
             vox._ptr(self.scene_base), vox._ptr(self.ws), self.ws.numel(), vox._ptr(self.status),
             vox._stream(stream))
         if st != vox.OK:
-            raise vox.VoxError(st, "vox_generate_batched")
+            raise vox.VoxError(st, "vox_generate_batched_ex")
 
     def clear_volumes(self):
         for m in self.masks:
@@ -83,10 +85,12 @@ class Batch:
         return self.lst[int(b[k]):int(b[k + 1])]
 
 
-def make_batch(workloads_list, flags=vox.OUT_LIST32 | vox.OUT_BITMASK, device="cuda") -> Batch:
+def make_batch(workloads_list, flags=vox.OUT_LIST32 | vox.OUT_BITMASK, device="cuda", bricks=True) -> Batch:
     """Upload scenes (workloads.Workload objects) as one batch. The list is sized
     exactly (from the segments' voxel counts, summed here on the host from the
-    same input bytes; the device recounts and checks the capacity)."""
+    same input bytes; the device recounts and checks the capacity). With
+    ``bricks`` (and every scene's width a multiple of 32) the volumes are built
+    by bricks, the workspace sized by vox_plan_batched."""
     import torch
 
     segs_np = np.ascontiguousarray(np.concatenate([w.segs for w in workloads_list], axis=0), dtype=np.int32)
@@ -107,11 +111,23 @@ def make_batch(workloads_list, flags=vox.OUT_LIST32 | vox.OUT_BITMASK, device="c
     elif flags & vox.OUT_LIST32:
         lst = torch.empty(max(V, 1), dtype=torch.int32, device=device)
     n_scenes = len(workloads_list)
-    ws = torch.empty(vox.vox_workspace_size_batched(len(segs_np), n_scenes), dtype=torch.uint8, device=device)
-    return Batch(segs=torch.from_numpy(segs_np).to(device), scenes=scenes, n_scenes=n_scenes, dims=dims,
-                 seg_counts=seg_counts, masks=masks, lst=lst,
-                 scene_base=torch.zeros(n_scenes + 1, dtype=torch.int64, device=device), ws=ws,
-                 status=torch.zeros(1, dtype=torch.int32, device=device), flags=flags, V=V)
+    d_segs = torch.from_numpy(segs_np).to(device)
+    status = torch.zeros(1, dtype=torch.int32, device=device)
+    per_scene = [vox.vox_scene_bricks(dm) for dm in dims]
+    total_bricks = sum(per_scene) if (bricks and flags & vox.OUT_BITMASK and len(segs_np) and
+                                      all(b > 0 for b in per_scene)) else 0
+    pieces = 0
+    if total_bricks:
+        ws = torch.empty(vox.vox_workspace_size_batched_volume(len(segs_np), n_scenes, total_bricks, 0),
+                         dtype=torch.uint8, device=device)
+        _, pieces = vox.vox_plan_batched(d_segs, scenes, n_scenes, total_bricks, ws, status)
+        size = vox.vox_workspace_size_batched_volume(len(segs_np), n_scenes, total_bricks, pieces)
+    else:
+        size = vox.vox_workspace_size_batched(len(segs_np), n_scenes)
+    ws = torch.empty(size, dtype=torch.uint8, device=device)
+    return Batch(segs=d_segs, scenes=scenes, n_scenes=n_scenes, dims=dims, seg_counts=seg_counts, masks=masks,
+                 lst=lst, scene_base=torch.zeros(n_scenes + 1, dtype=torch.int64, device=device), ws=ws,
+                 status=status, flags=flags, V=V, total_bricks=total_bricks, pieces=pieces)
 
 
 class GraphRunner:

@@ -153,50 +153,12 @@ vox_status check_generate_args(const vox_segment *segs, int64_t n, vox_dims dims
 }
 
 // ---- the volume by brick ownership ------------------------------------------
-constexpr int64_t kMaxBricks = int64_t(1) << 26;
 
-// Brick shape for a volume whose rows are whole 32-bit words (w % 32 == 0):
-// B0 = the largest 32 * 2^k not above min(w, 256) voxels along x (whole words),
-// then B1 x B2 rows (powers of two) so that a brick has at most kBrickWordsMax
-// words: 256 x 64 x 64 (128 KB) for wide volumes. Two things set the shape:
-// segments in random directions cross the fewer brick faces the more cube-like
-// and large the brick is (fewer pieces), and the brick's store writes one
-// request per brick row, so rows of 32 bytes (B0 = 256) store about three times
-// faster than rows of 16 bytes (measured: 18 against 56 us per 128 MiB volume).
+// The brick geometry of a single volume (brick_geom, with counter replicas).
 bool make_geom(vox_dims dims, BrickGeom *G)
 {
-    if (check_dims(dims) != VOX_OK || dims.w % 32 != 0) return false;
-    int32_t b0 = 32;
-    while (2 * b0 <= dims.w && 2 * b0 <= 256) b0 *= 2;
-    G->B[0] = b0;
-    G->bxw = b0 / 32;
-    G->log_bxw = 0;
-    while ((1 << G->log_bxw) < G->bxw) ++G->log_bxw;
-    const int32_t rows = kBrickWordsMax / G->bxw;
-    int32_t p2 = 1;
-    while ((2 * p2) * (2 * p2) <= rows) p2 *= 2;
-    G->B[1] = (2 * p2 * p2 <= rows) ? 2 * p2 : p2;
-    G->B[2] = p2;
-    G->log_b1 = 0;
-    while ((1 << G->log_b1) < G->B[1]) ++G->log_b1;
-    G->dim[0] = dims.w;
-    G->dim[1] = dims.h;
-    G->dim[2] = dims.d;
-    G->row_words = dims.w / 32;
-    G->words = G->bxw * G->B[1] * G->B[2];
-    for (int a = 0; a < 3; ++a) {
-        G->logB[a] = 0;
-        while ((1 << G->logB[a]) < G->B[a]) ++G->logB[a];
-    }
-    int64_t nb = 1;
-    for (int a = 0; a < 3; ++a) {
-        G->nb[a] = (G->dim[a] + G->B[a] - 1) / G->B[a];
-        nb *= G->nb[a];
-    }
-    G->n_bricks = nb;
-    G->reps = nb <= 32768 ? 8 : 1;
-    G->n_slots = nb * kPieceClasses * G->reps;
-    return nb <= kMaxBricks && G->words <= kBrickWordsMax;
+    if (check_dims(dims) != VOX_OK) return false;
+    return brick_geom(dims.w, dims.h, dims.d, G, true);
 }
 
 // Tensor map of the volume as a 3-D array of 32-bit words (row_words x h x d)
@@ -570,6 +532,99 @@ BatchLayout batch_layout(int64_t n_total, int32_t n_scenes)
     return B;
 }
 
+// Batched volumes by bricks: the batched layout, then every scene's brick
+// numbering, then the brick arrays over all scenes' slots and the pieces.
+struct BatchBrickLayout {
+    size_t sb;      // SceneBricks [n_scenes]
+    VolLayout VL;   // slots = total_bricks * kPieceClasses
+    BrickGeom tot;  // n_bricks and n_slots of the whole batch (the rest unused)
+};
+
+BatchBrickLayout batch_brick_layout(int64_t n_total, int32_t n_scenes, int64_t total_bricks, int64_t capacity)
+{
+    BatchBrickLayout L;
+    std::memset(&L.tot, 0, sizeof(L.tot));
+    L.tot.n_bricks = total_bricks;
+    L.tot.n_slots = total_bricks * kPieceClasses;
+    L.tot.reps = 1;
+    L.sb = batch_layout(n_total, n_scenes).total;
+    L.VL = vol_layout(n_total, L.tot, capacity, L.sb + align_up(sizeof(SceneBricks) * static_cast<size_t>(n_scenes)));
+    return L;
+}
+
+// The batched volumes by bricks: scene numbering, bin count, scan of the slot
+// counts, scatter, one CTA per brick (plain-store merge into its scene's
+// volume), then the batched atomics, run only if the pieces did not fit.
+vox_status launch_batched_bricks(const vox_segment *segs, int64_t n_total, const SceneDesc *scenes,
+                                 const int32_t *scene_of, int32_t n_scenes, int64_t total_bricks, bool fresh,
+                                 void *ws, size_t ws_bytes, int32_t *status, cudaStream_t stream, bool count_only)
+{
+    const BatchBrickLayout BL = batch_brick_layout(n_total, n_scenes, total_bricks, 0);
+    const VolLayout &VL = BL.VL;
+    const int64_t capacity = static_cast<int64_t>((ws_bytes - VL.pieces) / 8);
+    char *base = static_cast<char *>(ws);
+    SceneBricks *sb = reinterpret_cast<SceneBricks *>(base + BL.sb);
+    k_scene_bricks<<<1, 1, 0, stream>>>(scenes, n_scenes, sb, total_bricks, status);
+    if (cudaGetLastError() != cudaSuccess) return VOX_ERR_CUDA;
+    if (cudaMemsetAsync(base + VL.hdr, 0, VL.off - VL.hdr, stream) != cudaSuccess) return VOX_ERR_CUDA;
+    BinParams bp{};
+    bp.segs = reinterpret_cast<const int32_t *>(segs);
+    bp.n = n_total;
+    bp.G = BL.tot;
+    bp.brick_count = reinterpret_cast<int32_t *>(base + VL.count);
+    bp.cursor = reinterpret_cast<int64_t *>(base + VL.cursor);
+    bp.brick_off = reinterpret_cast<const int64_t *>(base + VL.off);
+    bp.pieces = reinterpret_cast<uint64_t *>(base + VL.pieces);
+    bp.capacity = capacity;
+    bp.status = status;
+    bp.sb = sb;
+    bp.scene_of = scene_of;
+    bp.n_scenes = n_scenes;
+    const unsigned bin_blocks = static_cast<unsigned>((n_total + 255) / 256);
+    k_bin_count<false, true><<<bin_blocks, 256, 0, stream>>>(bp);
+    ScanParams sp{};
+    sp.counts_in = bp.brick_count;
+    sp.offsets_copy = bp.cursor;
+    sp.n = BL.tot.n_slots;
+    sp.offsets = reinterpret_cast<int64_t *>(base + VL.off);
+    sp.desc = reinterpret_cast<uint64_t *>(base + VL.desc);
+    sp.ticket = reinterpret_cast<uint32_t *>(base + VL.hdr);
+    sp.status = status;
+    sp.n_tiles = VL.n_tiles;
+    sp.stall_tile = -1;
+    sp.wait_ns = static_cast<uint64_t>(g_wait_ns.load());
+    k_scan<false><<<static_cast<unsigned>(VL.n_tiles), kScanThreads, 0, stream>>>(sp);
+    if (cudaGetLastError() != cudaSuccess) return VOX_ERR_CUDA;
+    if (count_only) return VOX_OK;
+    k_bin_scatter<false, true><<<bin_blocks, 256, 0, stream>>>(bp);
+    BrickParams brp{};
+    brp.segs = bp.segs;
+    brp.G = BL.tot;
+    brp.brick_off = bp.brick_off;
+    brp.pieces = bp.pieces;
+    brp.capacity = capacity;
+    brp.mask = nullptr;
+    brp.status = status;
+    brp.ticket = reinterpret_cast<uint32_t *>(base + VL.hdr + 128);
+    brp.use_tma = 0;
+    brp.fresh = fresh ? 1 : 0;
+    brp.bricked = 0;
+    brp.sb = sb;
+    brp.n_scenes = n_scenes;
+    CUtensorMap tmap;
+    std::memset(&tmap, 0, sizeof(tmap));
+    const size_t bsmem = sizeof(BrickSmem);
+    const void *bk = reinterpret_cast<const void *>(k_brick_volume<false, true>);
+    if (vox_status e = allow_smem(bk, bsmem)) return e;
+    const int bgrid = grid_ctas(bk, kBrickThreads, bsmem);
+    if (bgrid <= 0) return VOX_ERR_CUDA;
+    k_brick_volume<false, true><<<static_cast<unsigned>(bgrid), kBrickThreads, bsmem, stream>>>(brp, tmap);
+    if (cudaGetLastError() != cudaSuccess) return VOX_ERR_CUDA;
+    const vox_dims unused{1, 1, 1};
+    return launch_generate(segs, n_total, unused, nullptr, 0, nullptr, VOX_OUT_BITMASK, ws, status, stream,
+                           bp.brick_off + BL.tot.n_slots, capacity, scenes, scene_of, n_scenes);
+}
+
 // ---- allocation-free variant: scratch in a static device array -------------
 // Same layout as ws_layout(VOX_NOALLOC_MAX_SEGMENTS): ticket region, tile
 // descriptors, offsets; each region rounded up to 256 bytes.
@@ -857,10 +912,12 @@ size_t vox_workspace_size_batched(int64_t n_total, int32_t n_scenes)
     return batch_layout(n_total, n_scenes).total;
 }
 
-vox_status vox_generate_batched(const vox_segment *d_segs, int64_t n_total, const vox_scene *d_scenes,
-                                int32_t n_scenes, void *d_list, int64_t list_capacity, int flags,
-                                int64_t *d_scene_base, void *d_ws, size_t ws_bytes, int32_t *d_status, void *stream)
+vox_status vox_generate_batched_ex(const vox_segment *d_segs, int64_t n_total, const vox_scene *d_scenes,
+                                   int32_t n_scenes, int64_t total_bricks, void *d_list, int64_t list_capacity,
+                                   int flags, int64_t *d_scene_base, void *d_ws, size_t ws_bytes, int32_t *d_status,
+                                   void *stream)
 {
+    if (total_bricks < 0) return VOX_ERR_INVALID_ARG;
     if (n_total < 0 || n_scenes < 1 || d_scenes == nullptr || d_status == nullptr) return VOX_ERR_INVALID_ARG;
     if (n_total > 0 && d_segs == nullptr) return VOX_ERR_INVALID_ARG;
     if (flags & ~(VOX_OUT_LIST32 | VOX_OUT_LIST64 | VOX_OUT_BITMASK | VOX_OUT_FRESH)) return VOX_ERR_INVALID_ARG;
@@ -873,6 +930,10 @@ vox_status vox_generate_batched(const vox_segment *d_segs, int64_t n_total, cons
     if (!aligned(d_scenes, 8)) return VOX_ERR_ALIGNMENT;
     const BatchLayout B = batch_layout(n_total, n_scenes);
     if (d_ws == nullptr || !aligned(d_ws, kWsAlign) || ws_bytes < B.total) return VOX_ERR_WORKSPACE;
+    // the volumes by bricks when the caller gave the batch's brick count and the
+    // workspace holds the brick arrays and a piece
+    const bool bricks = bm && total_bricks > 0 && n_total > 0 && n_total < (int64_t(1) << 32) &&
+                        ws_bytes >= batch_brick_layout(n_total, n_scenes, total_bricks, 1).VL.total;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     char *base = static_cast<char *>(d_ws);
     const SceneDesc *scenes = reinterpret_cast<const SceneDesc *>(d_scenes);
@@ -881,7 +942,7 @@ vox_status vox_generate_batched(const vox_segment *d_segs, int64_t n_total, cons
     k_scene_map<<<static_cast<unsigned>(n_scenes), 256, 0, s>>>(scenes, n_scenes, n_total, scene_of, d_status,
                                                                  l32 ? 1 : 0);
     if (cudaGetLastError() != cudaSuccess) return VOX_ERR_CUDA;
-    if (bm && (flags & VOX_OUT_FRESH)) {  // every scene's volume cleared (a valid table only)
+    if (bm && (flags & VOX_OUT_FRESH) && !bricks) {  // every scene's volume cleared (a valid table only)
         k_scene_clear<<<dim3(kSceneClearCtas, static_cast<unsigned>(n_scenes)), 256, 0, s>>>(scenes, d_status);
         if (cudaGetLastError() != cudaSuccess) return VOX_ERR_CUDA;
     }
@@ -906,12 +967,86 @@ vox_status vox_generate_batched(const vox_segment *d_segs, int64_t n_total, cons
                                            flags & (VOX_OUT_LIST32 | VOX_OUT_LIST64), d_ws, d_status, s))
             return e;
     }
+    if (bm && bricks)
+        return launch_batched_bricks(d_segs, n_total, scenes, scene_of, n_scenes, total_bricks,
+                                     (flags & VOX_OUT_FRESH) != 0, d_ws, ws_bytes, d_status, s, false);
     if (bm) {
         if (vox_status e = launch_generate(d_segs, n_total, unused, nullptr, 0, nullptr, VOX_OUT_BITMASK, d_ws, d_status,
                                            s, nullptr, 0, scenes, scene_of, n_scenes))
             return e;
     }
     return VOX_OK;
+}
+
+vox_status vox_generate_batched(const vox_segment *d_segs, int64_t n_total, const vox_scene *d_scenes,
+                                int32_t n_scenes, void *d_list, int64_t list_capacity, int flags,
+                                int64_t *d_scene_base, void *d_ws, size_t ws_bytes, int32_t *d_status, void *stream)
+{
+    return vox_generate_batched_ex(d_segs, n_total, d_scenes, n_scenes, 0, d_list, list_capacity, flags, d_scene_base,
+                                   d_ws, ws_bytes, d_status, stream);
+}
+
+int64_t vox_scene_bricks(vox_dims dims)
+{
+    BrickGeom G;
+    if (check_dims(dims) != VOX_OK || !brick_geom(dims.w, dims.h, dims.d, &G, false)) return 0;
+    return G.n_bricks;
+}
+
+size_t vox_workspace_size_batched_volume(int64_t n_total, int32_t n_scenes, int64_t total_bricks,
+                                         int64_t piece_capacity)
+{
+    if (n_total < 0 || n_scenes < 1 || total_bricks < 0 || piece_capacity < 0) return 0;
+    if (total_bricks == 0) return batch_layout(n_total, n_scenes).total;
+    return batch_brick_layout(n_total, n_scenes, total_bricks, piece_capacity > 0 ? piece_capacity : 1).VL.total;
+}
+
+vox_status vox_plan_batched(const vox_segment *d_segs, int64_t n_total, const vox_scene *d_scenes, int32_t n_scenes,
+                            int64_t total_bricks, void *d_ws, size_t ws_bytes, int32_t *d_status, int64_t *h_voxels,
+                            int64_t *h_pieces, void *stream)
+{
+    if (n_total < 0 || n_scenes < 1 || total_bricks < 0 || d_scenes == nullptr || d_status == nullptr)
+        return VOX_ERR_INVALID_ARG;
+    if (n_total > 0 && (d_segs == nullptr || !aligned(d_segs, 16))) return VOX_ERR_INVALID_ARG;
+    if (!aligned(d_scenes, 8)) return VOX_ERR_ALIGNMENT;
+    const bool bricks = total_bricks > 0 && n_total > 0 && n_total < (int64_t(1) << 32);
+    const size_t need = bricks ? batch_brick_layout(n_total, n_scenes, total_bricks, 0).VL.total
+                               : batch_layout(n_total, n_scenes).total;
+    if (d_ws == nullptr || !aligned(d_ws, kWsAlign) || ws_bytes < need) return VOX_ERR_WORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char *base = static_cast<char *>(d_ws);
+    const BatchLayout B = batch_layout(n_total, n_scenes);
+    const SceneDesc *scenes = reinterpret_cast<const SceneDesc *>(d_scenes);
+    int32_t *scene_of = reinterpret_cast<int32_t *>(base + B.scene_of);
+    if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), s) != cudaSuccess) return VOX_ERR_CUDA;
+    k_scene_map<<<static_cast<unsigned>(n_scenes), 256, 0, s>>>(scenes, n_scenes, n_total, scene_of, d_status, 0);
+    if (cudaGetLastError() != cudaSuccess) return VOX_ERR_CUDA;
+    int64_t V = 0, pieces = 0;
+    int32_t st = 0;
+    if (n_total > 0) {
+        const vox_dims unused{1, 1, 1};
+        if (vox_status e = launch_count_scan(d_segs, n_total, unused, nullptr, nullptr, d_ws, ws_bytes, d_status, s,
+                                             scenes, scene_of, n_scenes))
+            return e;
+        if (bricks) {
+            if (vox_status e = launch_batched_bricks(d_segs, n_total, scenes, scene_of, n_scenes, total_bricks, false,
+                                                     d_ws, ws_bytes, d_status, s, true))
+                return e;
+            const BatchBrickLayout BL = batch_brick_layout(n_total, n_scenes, total_bricks, 0);
+            if (cudaMemcpyAsync(&pieces, base + BL.VL.off + 8 * static_cast<size_t>(BL.tot.n_slots), 8,
+                                cudaMemcpyDeviceToHost, s) != cudaSuccess)
+                return VOX_ERR_CUDA;
+        }
+        if (cudaMemcpyAsync(&V, base + ws_layout(n_total).offsets + 8 * static_cast<size_t>(n_total), 8,
+                            cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return VOX_ERR_CUDA;
+    }
+    if (cudaMemcpyAsync(&st, d_status, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return VOX_ERR_CUDA;
+    if (h_voxels) *h_voxels = V;
+    if (h_pieces) *h_pieces = pieces;
+    return static_cast<vox_status>(st);
 }
 
 int64_t vox_mask_words_bricked(vox_dims dims)

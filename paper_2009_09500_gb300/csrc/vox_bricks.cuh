@@ -59,6 +59,62 @@ struct BrickGeom {
 };
 
 constexpr int kPieceClasses = 22;  // half octaves of the piece length (<= 1024)
+constexpr int64_t kMaxBricks = int64_t(1) << 26;
+
+// Brick shape for a volume whose rows are whole 32-bit words (w % 32 == 0):
+// B0 = the largest 32 * 2^k not above min(w, 256) voxels along x (whole words),
+// then B1 x B2 rows (powers of two) so that a brick has at most kBrickWordsMax
+// words: 256 x 64 x 64 (128 KB) for wide volumes. Two things set the shape:
+// segments in random directions cross the fewer brick faces the more cube-like
+// and large the brick is (fewer pieces), and the brick's store writes one
+// request per brick row, so rows of 32 bytes (B0 = 256) store about three times
+// faster than rows of 16 bytes (measured: 18 against 56 us per 128 MiB volume).
+// replicas: 8 counter replicas per (brick, class) when there are few bricks
+// (a single scene), else 1 (and always 1 inside a batch of scenes).
+__host__ __device__ inline bool brick_geom(int32_t w, int32_t h, int32_t d, BrickGeom *G, bool replicas)
+{
+    if (w < 1 || h < 1 || d < 1 || w % 32 != 0) return false;
+    int32_t b0 = 32;
+    while (2 * b0 <= w && 2 * b0 <= 256) b0 *= 2;
+    G->B[0] = b0;
+    G->bxw = b0 / 32;
+    G->log_bxw = 0;
+    while ((1 << G->log_bxw) < G->bxw) ++G->log_bxw;
+    const int32_t rows = kBrickWordsMax / G->bxw;
+    int32_t p2 = 1;
+    while ((2 * p2) * (2 * p2) <= rows) p2 *= 2;
+    G->B[1] = (2 * p2 * p2 <= rows) ? 2 * p2 : p2;
+    G->B[2] = p2;
+    G->log_b1 = 0;
+    while ((1 << G->log_b1) < G->B[1]) ++G->log_b1;
+    G->dim[0] = w;
+    G->dim[1] = h;
+    G->dim[2] = d;
+    G->row_words = w / 32;
+    G->words = G->bxw * G->B[1] * G->B[2];
+    for (int a = 0; a < 3; ++a) {
+        G->logB[a] = 0;
+        while ((1 << G->logB[a]) < G->B[a]) ++G->logB[a];
+    }
+    int64_t nb = 1;
+    for (int a = 0; a < 3; ++a) {
+        G->nb[a] = (G->dim[a] + G->B[a] - 1) / G->B[a];
+        nb *= G->nb[a];
+    }
+    G->n_bricks = nb;
+    G->reps = (replicas && nb <= 32768) ? 8 : 1;
+    G->n_slots = nb * kPieceClasses * G->reps;
+    return nb <= kMaxBricks && G->words <= kBrickWordsMax;
+}
+
+// A scene of a batch as the brick path sees it: its geometry (one replica), its
+// first brick and first slot in the batch's numbering, and its volume.
+struct SceneBricks {
+    BrickGeom G;
+    int64_t brick_base;
+    int64_t slot_base;
+    uint32_t *mask;
+};
 
 // Length class of a piece, longest first: 0 for the longest half octave.
 __device__ __forceinline__ int32_t piece_class_desc(int32_t len)
@@ -199,7 +255,27 @@ struct BinParams {
     uint64_t *pieces;         // [capacity]
     int64_t capacity;
     const int32_t *status;
+    const SceneBricks *sb;    // batched: each scene's geometry and numbering (else null)
+    const int32_t *scene_of;  // batched: scene of every segment
+    int32_t n_scenes;
 };
+
+// The geometry a segment's pieces follow and the first slot of its volume, or
+// null for a segment outside every scene (only after a table error, which the
+// status word holds; the batched kernels check it first).
+template <bool kBatched>
+__device__ __forceinline__ const BrickGeom *segment_geom(const BinParams &p, int64_t s, int64_t &slot_base)
+{
+    if constexpr (kBatched) {
+        const int32_t k = __ldg(p.scene_of + s);
+        if (static_cast<uint32_t>(k) >= static_cast<uint32_t>(p.n_scenes)) return nullptr;
+        slot_base = p.sb[k].slot_base;
+        return &p.sb[k].G;
+    } else {
+        slot_base = 0;
+        return &p.G;
+    }
+}
 
 __device__ __forceinline__ void load_record(const int32_t *segs, int64_t s, int32_t *r)
 {
@@ -209,38 +285,50 @@ __device__ __forceinline__ void load_record(const int32_t *segs, int64_t s, int3
 }
 
 // One segment per thread.
-template <bool kEuclid>
+template <bool kEuclid, bool kBatched = false>
 __global__ void __launch_bounds__(256) k_bin_count(BinParams p)
 {
-    // no status check: this pass may run beside the count + scan that resets the
-    // status word; it only writes the slot counts, and segments with endpoints
-    // outside the volume (reported by the count kernel) are skipped
+    // single volume: no status check (this pass may run beside the count + scan
+    // that resets the status word); it reads only the segments and the host's
+    // geometry, writes only the slot counts, and skips segments with endpoints
+    // outside the volume (reported by the count kernel)
     const int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (s >= p.n) return;
+    // a batch reads the scene map and numbering, valid only without an error
+    if (kBatched && ld_volatile_i32(p.status) != 0) return;
+    int64_t slot_base;
+    const BrickGeom *Gp = segment_geom<kBatched>(p, s, slot_base);
+    if (Gp == nullptr) return;
+    const BrickGeom &G = *Gp;
     int32_t r[6];
     load_record(p.segs, s, r);
-    if (!endpoints_inside(r, p.G)) return;
-    const int32_t rep = static_cast<int32_t>(s) & (p.G.reps - 1);
-    for_each_piece<kEuclid>(r, p.G, [&](int32_t b, int32_t, int32_t len) {
-        atomicAdd(p.brick_count + piece_slot(p.G, b, len, rep), 1);
+    if (!endpoints_inside(r, G)) return;
+    const int32_t rep = static_cast<int32_t>(s) & (G.reps - 1);
+    for_each_piece<kEuclid>(r, G, [&](int32_t b, int32_t, int32_t len) {
+        atomicAdd(p.brick_count + slot_base + piece_slot(G, b, len, rep), 1);
     });
 }
 
-// One segment per thread.
-template <bool kEuclid>
+// One segment per thread. p.G.n_slots: the number of slots (all scenes' when batched).
+template <bool kEuclid, bool kBatched = false>
 __global__ void __launch_bounds__(256) k_bin_scatter(BinParams p)
 {
+    using SlotT = typename std::conditional<kBatched, int64_t, uint32_t>::type;
     const int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (s >= p.n || ld_volatile_i32(p.status) != 0) return;
     if (__ldg(p.brick_off + p.G.n_slots) > p.capacity) return;  // the volume falls back to atomics
-    const int32_t rep = static_cast<int32_t>(s) & (p.G.reps - 1);
+    int64_t slot_base;
+    const BrickGeom *Gp = segment_geom<kBatched>(p, s, slot_base);
+    if (Gp == nullptr) return;
+    const BrickGeom &G = *Gp;
+    const int32_t rep = static_cast<int32_t>(s) & (G.reps - 1);
     int32_t r[6];
     load_record(p.segs, s, r);
-    if (!endpoints_inside(r, p.G)) return;
+    if (!endpoints_inside(r, G)) return;
     // slot reservations of up to four pieces are in flight together before
     // their stores, so the returning atomics' latency overlaps
     constexpr int kBatch = 4;
-    uint32_t bb[kBatch];
+    SlotT bb[kBatch];
     uint64_t val[kBatch];
     int nb = 0;
     auto flush = [&]() {
@@ -253,11 +341,11 @@ __global__ void __launch_bounds__(256) k_bin_scatter(BinParams p)
             if (e < nb) p.pieces[pos[e]] = val[e];
         nb = 0;
     };
-    for_each_piece<kEuclid>(r, p.G, [&](int32_t b, int32_t k, int32_t len) {
+    for_each_piece<kEuclid>(r, G, [&](int32_t b, int32_t k, int32_t len) {
 #pragma unroll
         for (int e = 0; e < kBatch; ++e)
             if (e == nb) {
-                bb[e] = piece_slot(p.G, b, len, rep);
+                bb[e] = static_cast<SlotT>(slot_base + piece_slot(G, b, len, rep));
                 val[e] = pack_piece(s, k, len);
             }
         if (++nb == kBatch) flush();
@@ -277,6 +365,8 @@ struct BrickParams {
     int32_t use_tma;   // merge by one TMA tensor reduce-OR (or store) per brick (tensor map valid)
     int32_t fresh;     // write every brick (zeros included) instead of OR-ing into the volume
     int32_t bricked;   // brick-major volume: brick b is words `words` at mask + b * words (one bulk copy)
+    const SceneBricks *sb;  // batched: each scene's geometry, numbering and volume (G.n_slots,
+    int32_t n_scenes;       // G.n_bricks: the batch's totals; merged by plain stores)
 };
 
 // TMA tensor reduction of a whole brick tile from shared memory into the volume:
@@ -364,6 +454,9 @@ struct BrickSmem {
     int32_t origin[3];
     int32_t next_group;  // next group of 32 pieces of the brick to hand to a warp
     int64_t brick;
+    int64_t first_slot;  // the brick's first slot
+    BrickGeom geom;      // batched: the brick's scene geometry
+    uint32_t *bmask;     // batched: the scene's volume
 };
 
 // One CTA per brick (dynamic tickets). The brick's pieces arrive ordered by
@@ -374,7 +467,7 @@ struct BrickSmem {
 // record, enters the segment at the piece's first step (one division per minor
 // axis) and steps through the piece with the carry recurrence, OR-ing bits into
 // the brick's shared bitmap; the bitmap is then merged into the volume.
-template <bool kEuclid>
+template <bool kEuclid, bool kBatched = false>
 __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, const __grid_constant__ CUtensorMap tmap)
 {
     extern __shared__ __align__(128) unsigned char brick_smem_raw[];
@@ -391,28 +484,46 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
     }
     if (overflow && !p.fresh) return;
     const bool async_store = p.use_tma || p.bricked;  // the bitmap leaves by the bulk-copy unit
-    const BrickGeom &G = p.G;
-    const int64_t slots_per_brick = static_cast<int64_t>(kPieceClasses) * G.reps;
-    const uint32_t bw = static_cast<uint32_t>(G.B[0]);
-    const uint32_t bwh = static_cast<uint32_t>(G.B[0]) * static_cast<uint32_t>(G.B[1]);
+    const int64_t total_bricks = p.G.n_bricks;
     while (true) {
         if (t == 0) {
             const int64_t b = atomicAdd(p.ticket, 1u);
             sm.brick = b;
             sm.next_group = 0;
-            if (b < G.n_bricks) {
-                const int64_t rest = b / G.nb[0];
-                sm.origin[0] = static_cast<int32_t>(b - rest * G.nb[0]) * G.B[0];
-                sm.origin[1] = static_cast<int32_t>(rest % G.nb[1]) * G.B[1];
-                sm.origin[2] = static_cast<int32_t>(rest / G.nb[1]) * G.B[2];
+            if (b < total_bricks) {
+                int64_t lb = b;  // the brick's index in its volume
+                const BrickGeom *Gt = &p.G;
+                if constexpr (kBatched) {  // the scene holding brick b: last with brick_base <= b
+                    int32_t lo_s = 0, hi_s = p.n_scenes;
+                    while (hi_s - lo_s > 1) {
+                        const int32_t mid = (lo_s + hi_s) >> 1;
+                        if (p.sb[mid].brick_base <= b) lo_s = mid;
+                        else hi_s = mid;
+                    }
+                    sm.geom = p.sb[lo_s].G;
+                    sm.bmask = p.sb[lo_s].mask;
+                    lb = b - p.sb[lo_s].brick_base;
+                    sm.first_slot = p.sb[lo_s].slot_base + lb * kPieceClasses;
+                    Gt = &sm.geom;
+                } else {
+                    sm.first_slot = b * kPieceClasses * p.G.reps;
+                }
+                const int64_t rest = lb / Gt->nb[0];
+                sm.origin[0] = static_cast<int32_t>(lb - rest * Gt->nb[0]) * Gt->B[0];
+                sm.origin[1] = static_cast<int32_t>(rest % Gt->nb[1]) * Gt->B[1];
+                sm.origin[2] = static_cast<int32_t>(rest / Gt->nb[1]) * Gt->B[2];
             }
         }
         __syncthreads();
         const int64_t b = sm.brick;
+        if (b >= total_bricks) break;
+        const BrickGeom &G = kBatched ? sm.geom : p.G;
         const int32_t X0 = sm.origin[0], Y0 = sm.origin[1], Z0 = sm.origin[2];
-        if (b >= G.n_bricks) break;
-        const int64_t lo = overflow ? 0 : __ldg(p.brick_off + b * slots_per_brick);
-        const int64_t hi = overflow ? 0 : __ldg(p.brick_off + (b + 1) * slots_per_brick);
+        const uint32_t bw = static_cast<uint32_t>(G.B[0]);
+        const uint32_t bwh = static_cast<uint32_t>(G.B[0]) * static_cast<uint32_t>(G.B[1]);
+        const int64_t slots_per_brick = static_cast<int64_t>(kPieceClasses) * G.reps;
+        const int64_t lo = overflow ? 0 : __ldg(p.brick_off + sm.first_slot);
+        const int64_t hi = overflow ? 0 : __ldg(p.brick_off + sm.first_slot + slots_per_brick);
         if (lo == hi && !p.fresh) {
             __syncthreads();  // everyone has read the ticket slot before it is rewritten
             continue;
@@ -479,7 +590,8 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
                 else tma_reduce_or_3d(&tmap, sm.bits, X0 / 32, Y0, Z0);
             }
         } else {
-            merge_brick(sm.bits, G, X0, Y0, Z0, p.mask, p.fresh != 0);
+            uint32_t *const mask = kBatched ? sm.bmask : p.mask;
+            if (mask != nullptr) merge_brick(sm.bits, G, X0, Y0, Z0, mask, p.fresh != 0);
             __syncthreads();
         }
     }

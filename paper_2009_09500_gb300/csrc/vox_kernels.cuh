@@ -585,6 +585,30 @@ __global__ void __launch_bounds__(256) k_scene_clear(const SceneDesc *scenes, co
     if (tail0 + tid < words) sd.mask[tail0 + tid] = 0u;
 }
 
+// The brick numbering of a batch: every scene's geometry (one counter replica),
+// first brick and first slot, in scene order (one thread; scenes are few). A
+// scene that cannot take bricks, or a total that differs from the caller's,
+// is VOX_ERR_INVALID_ARG (nothing is written after it).
+__global__ void k_scene_bricks(const SceneDesc *scenes, int32_t n_scenes, SceneBricks *sb, int64_t total_bricks,
+                               int32_t *status)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0 || ld_volatile_i32(status) != 0) return;
+    int64_t next = 0;
+    for (int32_t k = 0; k < n_scenes; ++k) {
+        SceneBricks e;
+        if (!brick_geom(scenes[k].w, scenes[k].h, scenes[k].d, &e.G, false)) {
+            set_status(status, 1);  // VOX_ERR_INVALID_ARG
+            return;
+        }
+        e.brick_base = next;
+        e.slot_base = next * kPieceClasses;
+        e.mask = scenes[k].mask;
+        sb[k] = e;
+        next += e.G.n_bricks;
+    }
+    if (next != total_bricks) set_status(status, 1);
+}
+
 // First global voxel id of every scene (and V at index n_scenes).
 __global__ void k_scene_base(const SceneDesc *scenes, int32_t n_scenes, const int64_t *offsets, int64_t n_total,
                              int64_t *base, int64_t *base_out, const int32_t *status)

@@ -43,7 +43,8 @@ EXPORTED = (
     "vox_set_tuning", "vox_get_tuning", "vox_host_arena_size_volume",
     "vox_mask_words_bricked", "vox_brick_shape", "vox_unbrick",
     "vox_euclid_workspace_size", "vox_euclid_generate", "vox_euclid_plan", "vox_euclid_workspace_size_volume",
-    "vox_count_bins",
+    "vox_count_bins", "vox_scene_bricks", "vox_workspace_size_batched_volume", "vox_generate_batched_ex",
+    "vox_plan_batched",
 )
 
 VOLUME_AUTO = 0
@@ -133,6 +134,14 @@ def load(path: str | None = None):
     lib.vox_workspace_size_batched.restype = sz
     lib.vox_generate_batched.argtypes = [vp, i64, vp, ctypes.c_int32, vp, i64, i32, vp, vp, sz, vp, vp]
     lib.vox_generate_batched.restype = i32
+    lib.vox_scene_bricks.argtypes = [Dims]
+    lib.vox_scene_bricks.restype = i64
+    lib.vox_workspace_size_batched_volume.argtypes = [i64, ctypes.c_int32, i64, i64]
+    lib.vox_workspace_size_batched_volume.restype = sz
+    lib.vox_generate_batched_ex.argtypes = [vp, i64, vp, ctypes.c_int32, i64, vp, i64, i32, vp, vp, sz, vp, vp]
+    lib.vox_generate_batched_ex.restype = i32
+    lib.vox_plan_batched.argtypes = [vp, i64, vp, ctypes.c_int32, i64, vp, sz, vp, vp, vp, vp]
+    lib.vox_plan_batched.restype = i32
     lib.vox_set_tuning.argtypes = [vp]
     lib.vox_set_tuning.restype = None
     lib.vox_get_tuning.argtypes = [vp]
@@ -194,6 +203,25 @@ def vox_plan(segs, dims, ws, status, stream=None):
 
 def vox_workspace_size_batched(n_total: int, n_scenes: int) -> int:
     return int(load().vox_workspace_size_batched(int(n_total), int(n_scenes)))
+
+
+def vox_scene_bricks(dims) -> int:
+    return int(load().vox_scene_bricks(_dims(dims)))
+
+
+def vox_workspace_size_batched_volume(n_total: int, n_scenes: int, total_bricks: int, piece_capacity: int) -> int:
+    return int(load().vox_workspace_size_batched_volume(int(n_total), int(n_scenes), int(total_bricks),
+                                                        int(piece_capacity)))
+
+
+def vox_plan_batched(segs, scenes, n_scenes: int, total_bricks: int, ws, status, stream=None):
+    """Synchronous: (total voxels, brick pieces) of a batch."""
+    v, pc = ctypes.c_int64(0), ctypes.c_int64(0)
+    st = load().vox_plan_batched(_ptr(segs), segs.shape[0], _ptr(scenes), int(n_scenes), int(total_bricks), _ptr(ws),
+                                 ws.numel() * ws.element_size(), _ptr(status), ctypes.byref(v), ctypes.byref(pc),
+                                 _stream(stream))
+    _check(st, "vox_plan_batched")
+    return int(v.value), int(pc.value)
 
 
 def vox_set_tuning(run_len: int = 0, volume_path: int = 0, ctas_per_sm: int = 0) -> None:

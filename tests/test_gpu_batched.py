@@ -222,3 +222,40 @@ def test_count_bins_beside_the_scan():
     with pytest.raises(vox.VoxError) as e:
         vox.vox_count_bins(segs, w.dims, small)
     assert e.value.status == vox.ERR_WORKSPACE
+
+
+def test_batched_bricks_and_atomics_agree_with_oracle():
+    """The same scenes with the volumes by bricks (the default when every width
+    is a multiple of 32) and by atomics (bricks=False)."""
+    scenes = small_scenes(16, seed=46)
+    b = batching.make_batch(scenes)
+    assert b.total_bricks > 0 and b.pieces > 0
+    b.run()
+    check_scenes(b, scenes)
+    a = batching.make_batch(scenes, bricks=False)
+    assert a.total_bricks == 0
+    a.run()
+    check_scenes(a, scenes)
+
+
+def test_batched_bricks_pieces_do_not_fit():
+    """A brick workspace with room for 10 pieces: the batched atomics take over on
+    the device, same volumes (OR-into and fresh)."""
+    scenes = small_scenes(8, seed=47)
+    for flags in (vox.OUT_BITMASK, vox.OUT_LIST32 | vox.OUT_BITMASK | vox.OUT_FRESH):
+        b = batching.make_batch(scenes, flags=flags)
+        b.ws = torch.empty(vox.vox_workspace_size_batched_volume(int(b.segs.shape[0]), b.n_scenes, b.total_bricks, 10),
+                           dtype=torch.uint8, device="cuda")
+        for m in b.masks:
+            m.fill_(-1 if flags & vox.OUT_FRESH else 0)
+        b.run()
+        check_scenes(b, scenes)
+
+
+def test_batched_bricks_wrong_total_is_refused_on_the_device():
+    scenes = small_scenes(4, seed=48)
+    b = batching.make_batch(scenes)
+    b.total_bricks += 1
+    b.run()
+    torch.cuda.synchronize()
+    assert int(b.status.item()) == vox.ERR_INVALID_ARG
