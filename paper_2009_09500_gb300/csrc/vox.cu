@@ -933,6 +933,7 @@ vox_status vox_generate_batched_ex(const vox_segment *d_segs, int64_t n_total, c
     // the volumes by bricks when the caller gave the batch's brick count and the
     // workspace holds the brick arrays and a piece
     const bool bricks = bm && total_bricks > 0 && n_total > 0 && n_total < (int64_t(1) << 32) &&
+                        current_tuning().volume_path != VOX_VOLUME_ATOMIC &&
                         ws_bytes >= batch_brick_layout(n_total, n_scenes, total_bricks, 1).VL.total;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     char *base = static_cast<char *>(d_ws);

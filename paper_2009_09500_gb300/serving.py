@@ -45,9 +45,16 @@ class ServeRequest:
         return 4 * ((w * h * d + 31) // 32)
 
     @property
+    def piece_capacity(self) -> int:
+        """Room for brick pieces: a segment of L voxels has at most about 1 + 2L/64
+        pieces in 256 x 64 x 64 bricks; twice that covers random directions, and
+        pieces beyond it fall back to atomics on the device."""
+        return 2 * self.n + self.voxels // 16 + 1024
+
+    @property
     def device_bytes(self) -> int:
-        """Volume + segments + workspace share of this request on the device."""
-        return self.mask_bytes + 24 * self.n + 16 * self.n + 256
+        """Volume + segments + workspace share (with brick pieces) of this request."""
+        return self.mask_bytes + 24 * self.n + 16 * self.n + 8 * self.piece_capacity + 256
 
     @property
     def latency_ms(self) -> float:
@@ -214,10 +221,11 @@ class _Handle:
 
 
 class GpuLauncher:
-    """Launches a batch with vox_generate_batched (volumes only, VOX_OUT_FRESH)
-    on one of ``slots`` streams: segments copied from pinned host memory, new
-    volumes cleared by the launch, one scene table, one workspace, one
-    completion event."""
+    """Launches a batch with vox_generate_batched_ex (volumes only,
+    VOX_OUT_FRESH; by bricks when every request's width is a multiple of 32, the
+    piece room estimated from the requests' voxel counts) on one of ``slots``
+    streams: segments copied from pinned host memory, new volumes written whole
+    by the launch, one scene table, one workspace, one completion event."""
 
     def __init__(self, slots: int, device="cuda", keep_results: bool = False):
         import torch
@@ -246,14 +254,18 @@ class GpuLauncher:
                                                [m.data_ptr() for m in masks])
             scenes = torch.frombuffer(bytearray(table), dtype=torch.uint8).pin_memory().to(self.device,
                                                                                          non_blocking=True)
-            ws = torch.empty(vox.vox_workspace_size_batched(n_total, len(reqs)), dtype=torch.uint8,
-                             device=self.device)
+            per_scene = [vox.vox_scene_bricks(r.dims) for r in reqs]
+            total_bricks = sum(per_scene) if n_total and all(b > 0 for b in per_scene) else 0
+            ws = torch.empty(vox.vox_workspace_size_batched_volume(n_total, len(reqs), total_bricks,
+                                                                   sum(r.piece_capacity for r in reqs)),
+                             dtype=torch.uint8, device=self.device)
             status = torch.zeros(1, dtype=torch.int32, device=self.device)
-            st = vox.load().vox_generate_batched(
-                vox._ptr(segs), n_total, vox._ptr(scenes), len(reqs), None, 0, vox.OUT_BITMASK | vox.OUT_FRESH, None,
-                vox._ptr(ws), ws.numel(), vox._ptr(status), vox._stream(stream))
+            st = vox.load().vox_generate_batched_ex(
+                vox._ptr(segs), n_total, vox._ptr(scenes), len(reqs), total_bricks, None, 0,
+                vox.OUT_BITMASK | vox.OUT_FRESH, None, vox._ptr(ws), ws.numel(), vox._ptr(status),
+                vox._stream(stream))
             if st != vox.OK:
-                raise vox.VoxError(st, "vox_generate_batched")
+                raise vox.VoxError(st, "vox_generate_batched_ex")
             ev = torch.cuda.Event()
             ev.record(stream)
         keep = {"segs": segs, "masks": masks, "scenes": scenes, "ws": ws, "status": status}
