@@ -269,7 +269,7 @@ def aggregate_ranks(ms_local: float, voxels_local: int, world: int, device):
     return ms_max, total, total / (ms_max / 1000.0)
 
 
-def measure_batched(steps: int, dev) -> dict:
+def measure_batched(steps: int, dev, tune: bool = True) -> dict:
     """Batched vs plain launches on the 256-scene workload (uneven scenes, volume
     edges 64..512, 1e3..1e5 segments each; list32 + one volume per scene):
     one vox_generate_batched sequence (eager and replayed from a CUDA graph)
@@ -283,10 +283,13 @@ def measure_batched(steps: int, dev) -> dict:
     b = batching.make_batch(scenes, device=dev)
     plain = batching.PlainScenes(b, device=dev)
     # the launch tuning is process-wide: tune for this batch (its own workload class)
-    from paper_2009_09500_gb300 import autotune
+    from paper_2009_09500_gb300 import autotune, vox
 
-    tuning = autotune.get_or_tune(lambda: b.run(), int(b.segs.shape[0]), b.V, (512, 512, 512), b.flags | 0x100,
-                                  reps=3)
+    if tune:
+        tuning = autotune.get_or_tune(lambda: b.run(), int(b.segs.shape[0]), b.V, (512, 512, 512), b.flags | 0x100,
+                                      reps=3)
+    else:
+        tuning = {"params": vox.vox_get_tuning()}
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -673,7 +676,7 @@ def run_ours(args):
     batched = None
     main_tuning = vox.vox_get_tuning()
     if not args.no_batched and world == 1:
-        batched = measure_batched(args.steps, dev)  # tunes for the batch; serving keeps that tuning
+        batched = measure_batched(args.steps, dev, tune=not args.tuning)  # serving keeps the batch's tuning
     served = None
     if not args.no_serve and world == 1:
         served = measure_serving(args.serve_seconds, dev)

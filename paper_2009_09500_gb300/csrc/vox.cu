@@ -535,8 +535,9 @@ BatchLayout batch_layout(int64_t n_total, int32_t n_scenes)
 // Batched volumes by bricks: the batched layout, then every scene's brick
 // numbering, then the brick arrays over all scenes' slots and the pieces.
 struct BatchBrickLayout {
-    size_t sb;      // SceneBricks [n_scenes]
-    VolLayout VL;   // slots = total_bricks * kPieceClasses
+    size_t sb;           // SceneBricks [n_scenes]
+    size_t brick_scene;  // int32 [total_bricks]
+    VolLayout VL;        // slots = total_bricks * kPieceClasses
     BrickGeom tot;  // n_bricks and n_slots of the whole batch (the rest unused)
 };
 
@@ -548,7 +549,8 @@ BatchBrickLayout batch_brick_layout(int64_t n_total, int32_t n_scenes, int64_t t
     L.tot.n_slots = total_bricks * kPieceClasses;
     L.tot.reps = 1;
     L.sb = batch_layout(n_total, n_scenes).total;
-    L.VL = vol_layout(n_total, L.tot, capacity, L.sb + align_up(sizeof(SceneBricks) * static_cast<size_t>(n_scenes)));
+    L.brick_scene = L.sb + align_up(sizeof(SceneBricks) * static_cast<size_t>(n_scenes));
+    L.VL = vol_layout(n_total, L.tot, capacity, L.brick_scene + align_up(4 * static_cast<size_t>(total_bricks)));
     return L;
 }
 
@@ -564,7 +566,8 @@ vox_status launch_batched_bricks(const vox_segment *segs, int64_t n_total, const
     const int64_t capacity = static_cast<int64_t>((ws_bytes - VL.pieces) / 8);
     char *base = static_cast<char *>(ws);
     SceneBricks *sb = reinterpret_cast<SceneBricks *>(base + BL.sb);
-    k_scene_bricks<<<1, 1, 0, stream>>>(scenes, n_scenes, sb, total_bricks, status);
+    int32_t *brick_scene = reinterpret_cast<int32_t *>(base + BL.brick_scene);
+    k_scene_bricks<<<1, kSceneBrickThreads, 0, stream>>>(scenes, n_scenes, sb, brick_scene, total_bricks, status);
     if (cudaGetLastError() != cudaSuccess) return VOX_ERR_CUDA;
     if (cudaMemsetAsync(base + VL.hdr, 0, VL.off - VL.hdr, stream) != cudaSuccess) return VOX_ERR_CUDA;
     BinParams bp{};
@@ -611,6 +614,7 @@ vox_status launch_batched_bricks(const vox_segment *segs, int64_t n_total, const
     brp.bricked = 0;
     brp.sb = sb;
     brp.n_scenes = n_scenes;
+    brp.brick_scene = brick_scene;
     CUtensorMap tmap;
     std::memset(&tmap, 0, sizeof(tmap));
     const size_t bsmem = sizeof(BrickSmem);

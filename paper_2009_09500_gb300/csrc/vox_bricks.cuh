@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(256) k_bin_count(BinParams p)
     int64_t slot_base;
     const BrickGeom *Gp = segment_geom<kBatched>(p, s, slot_base);
     if (Gp == nullptr) return;
-    const BrickGeom &G = *Gp;
+    const BrickGeom G = *Gp;  // in registers: the atomics below cannot alias it
     int32_t r[6];
     load_record(p.segs, s, r);
     if (!endpoints_inside(r, G)) return;
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(256) k_bin_scatter(BinParams p)
     int64_t slot_base;
     const BrickGeom *Gp = segment_geom<kBatched>(p, s, slot_base);
     if (Gp == nullptr) return;
-    const BrickGeom &G = *Gp;
+    const BrickGeom G = *Gp;  // in registers: the atomics and stores below cannot alias it
     const int32_t rep = static_cast<int32_t>(s) & (G.reps - 1);
     int32_t r[6];
     load_record(p.segs, s, r);
@@ -365,8 +365,9 @@ struct BrickParams {
     int32_t use_tma;   // merge by one TMA tensor reduce-OR (or store) per brick (tensor map valid)
     int32_t fresh;     // write every brick (zeros included) instead of OR-ing into the volume
     int32_t bricked;   // brick-major volume: brick b is words `words` at mask + b * words (one bulk copy)
-    const SceneBricks *sb;  // batched: each scene's geometry, numbering and volume (G.n_slots,
-    int32_t n_scenes;       // G.n_bricks: the batch's totals; merged by plain stores)
+    const SceneBricks *sb;       // batched: each scene's geometry, numbering and volume (G.n_slots,
+    int32_t n_scenes;            // G.n_bricks: the batch's totals; merged by plain stores)
+    const int32_t *brick_scene;  // batched: the scene of every brick
 };
 
 // TMA tensor reduction of a whole brick tile from shared memory into the volume:
@@ -493,17 +494,12 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
             if (b < total_bricks) {
                 int64_t lb = b;  // the brick's index in its volume
                 const BrickGeom *Gt = &p.G;
-                if constexpr (kBatched) {  // the scene holding brick b: last with brick_base <= b
-                    int32_t lo_s = 0, hi_s = p.n_scenes;
-                    while (hi_s - lo_s > 1) {
-                        const int32_t mid = (lo_s + hi_s) >> 1;
-                        if (p.sb[mid].brick_base <= b) lo_s = mid;
-                        else hi_s = mid;
-                    }
-                    sm.geom = p.sb[lo_s].G;
-                    sm.bmask = p.sb[lo_s].mask;
-                    lb = b - p.sb[lo_s].brick_base;
-                    sm.first_slot = p.sb[lo_s].slot_base + lb * kPieceClasses;
+                if constexpr (kBatched) {  // the brick's scene and its geometry
+                    const int32_t k = __ldg(p.brick_scene + b);
+                    sm.geom = p.sb[k].G;
+                    sm.bmask = p.sb[k].mask;
+                    lb = b - p.sb[k].brick_base;
+                    sm.first_slot = p.sb[k].slot_base + lb * kPieceClasses;
                     Gt = &sm.geom;
                 } else {
                     sm.first_slot = b * kPieceClasses * p.G.reps;

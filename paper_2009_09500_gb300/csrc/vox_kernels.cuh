@@ -586,27 +586,52 @@ __global__ void __launch_bounds__(256) k_scene_clear(const SceneDesc *scenes, co
 }
 
 // The brick numbering of a batch: every scene's geometry (one counter replica),
-// first brick and first slot, in scene order (one thread; scenes are few). A
-// scene that cannot take bricks, or a total that differs from the caller's,
-// is VOX_ERR_INVALID_ARG (nothing is written after it).
-__global__ void k_scene_bricks(const SceneDesc *scenes, int32_t n_scenes, SceneBricks *sb, int64_t total_bricks,
-                               int32_t *status)
+// first brick and first slot, in scene order. One CTA: each thread takes a
+// chunk of consecutive scenes, a block scan of the chunks' brick counts gives
+// the chunks' first bricks. A scene that cannot take bricks, or a total that
+// differs from the caller's, is VOX_ERR_INVALID_ARG (nothing is written after).
+constexpr int kSceneBrickThreads = 256;
+__global__ void __launch_bounds__(kSceneBrickThreads) k_scene_bricks(const SceneDesc *scenes, int32_t n_scenes,
+                                                                    SceneBricks *sb, int32_t *brick_scene,
+                                                                    int64_t total_bricks, int32_t *status)
 {
-    if (blockIdx.x != 0 || threadIdx.x != 0 || ld_volatile_i32(status) != 0) return;
-    int64_t next = 0;
-    for (int32_t k = 0; k < n_scenes; ++k) {
+    __shared__ int64_t s_sum[kSceneBrickThreads];
+    __shared__ int32_t s_bad;
+    const int t = threadIdx.x;
+    if (ld_volatile_i32(status) != 0) return;  // uniform: the table was refused
+    if (t == 0) s_bad = 0;
+    __syncthreads();
+    const int32_t per = (n_scenes + kSceneBrickThreads - 1) / kSceneBrickThreads;
+    const int32_t k0 = min(n_scenes, t * per), k1 = min(n_scenes, k0 + per);
+    int64_t own = 0;
+    for (int32_t k = k0; k < k1; ++k) {  // geometry of the chunk; bases below
         SceneBricks e;
         if (!brick_geom(scenes[k].w, scenes[k].h, scenes[k].d, &e.G, false)) {
-            set_status(status, 1);  // VOX_ERR_INVALID_ARG
-            return;
+            s_bad = 1;
+            e.G.n_bricks = 0;
         }
-        e.brick_base = next;
-        e.slot_base = next * kPieceClasses;
         e.mask = scenes[k].mask;
         sb[k] = e;
-        next += e.G.n_bricks;
+        own += e.G.n_bricks;
     }
-    if (next != total_bricks) set_status(status, 1);
+    s_sum[t] = own;
+    __syncthreads();
+    for (int o = 1; o < kSceneBrickThreads; o <<= 1) {  // inclusive scan of the chunks' counts
+        const int64_t v = t >= o ? s_sum[t - o] : 0;
+        __syncthreads();
+        s_sum[t] += v;
+        __syncthreads();
+    }
+    const bool ok = !s_bad && s_sum[kSceneBrickThreads - 1] == total_bricks;
+    int64_t next = s_sum[t] - own;
+    for (int32_t k = k0; k < k1; ++k) {
+        sb[k].brick_base = next;
+        sb[k].slot_base = next * kPieceClasses;
+        if (ok)  // the scene of every brick (sized by total_bricks)
+            for (int64_t b = 0; b < sb[k].G.n_bricks; ++b) brick_scene[next + b] = k;
+        next += sb[k].G.n_bricks;
+    }
+    if (t == kSceneBrickThreads - 1 && !ok) set_status(status, 1);  // VOX_ERR_INVALID_ARG
 }
 
 // First global voxel id of every scene (and V at index n_scenes).
