@@ -524,6 +524,14 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
             __syncthreads();  // everyone has read the ticket slot before it is rewritten
             continue;
         }
+        const int64_t cnt = hi - lo;
+        // the warp's first group: its ticket and piece load go out before the bitmap
+        // clear and its record load after it, so that their latency overlaps the clear
+        int32_t grp = 0;
+        if (lane == 0) grp = atomicAdd(&sm.next_group, 1);
+        grp = __shfl_sync(0xffffffffu, grp, 0);
+        int64_t j = static_cast<int64_t>(grp) * 32 + lane;
+        uint64_t pc = j < cnt ? __ldg(p.pieces + lo + j) : 0ull;
         if (async_store) {  // the previous brick's copy must have read the tile
             if (t == 0) bulk_wait_read_all();
         }
@@ -532,24 +540,17 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
             uint4 *z = reinterpret_cast<uint4 *>(sm.bits);
             for (int q = t; q < G.words / 4; q += kBrickThreads) z[q] = make_uint4(0u, 0u, 0u, 0u);
         }
+        int32_t rec[6] = {0, 0, 0, 0, 0, 0};
+        if (j < cnt) load_record(p.segs, static_cast<int64_t>(pc & 0xffffffffull), rec);
         __syncthreads();
         // brick-local bit index of (x, y, z): (x - X0) + B0 (y - Y0) + B0 B1 (z - Z0),
         // kept modulo 2^32 while stepping (only the local value is ever used)
         const uint32_t origin = static_cast<uint32_t>(X0) + static_cast<uint32_t>(Y0) * bw +
                                 static_cast<uint32_t>(Z0) * bwh;
-        const int64_t cnt = hi - lo;
 #pragma unroll 1
-        while (true) {
-            int32_t grp = 0;
-            if (lane == 0) grp = atomicAdd(&sm.next_group, 1);
-            grp = __shfl_sync(0xffffffffu, grp, 0);
-            if (static_cast<int64_t>(grp) * 32 >= cnt) break;
-            const int64_t j = static_cast<int64_t>(grp) * 32 + lane;
+        while (static_cast<int64_t>(grp) * 32 < cnt) {
             if (j < cnt) {
-                const uint64_t pc = __ldg(p.pieces + lo + j);
                 const int32_t len = static_cast<int32_t>(pc >> 54) + 1;
-                int32_t rec[6];
-                load_record(p.segs, static_cast<int64_t>(pc & 0xffffffffull), rec);
                 using St = typename std::conditional<kEuclid, EuclidStepper<uint32_t, uint32_t>,
                                                      Stepper<uint32_t, uint32_t>>::type;
                 St st;
@@ -559,9 +560,9 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
                 // merge runs of the same word (measured on both workload shapes);
                 // repeated samples of the Euclidean variant set the same bit again
                 int32_t e = 0;
-                for (; e + 4 <= len; e += 4) {
+                for (; e + 8 <= len; e += 8) {
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) {
+                    for (int v = 0; v < 8; ++v) {
                         atomicOr(sm.bits + (st.L >> 5), 1u << (st.L & 31u));
                         st.template step<false, true>();
                     }
@@ -572,6 +573,13 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
                 }
             }
             __syncwarp();
+            if (lane == 0) grp = atomicAdd(&sm.next_group, 1);
+            grp = __shfl_sync(0xffffffffu, grp, 0);
+            j = static_cast<int64_t>(grp) * 32 + lane;
+            if (j < cnt) {
+                pc = __ldg(p.pieces + lo + j);
+                load_record(p.segs, static_cast<int64_t>(pc & 0xffffffffull), rec);
+            }
         }
         __syncthreads();
         if (p.bricked) {

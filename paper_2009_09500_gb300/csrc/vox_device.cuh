@@ -182,18 +182,6 @@ struct Stepper {
         const int32_t N = max(ax, max(ay, az));
         left = N - k;
         twoN = 2 * N;
-        int32_t qx = 0, qy = 0, qz = 0, rx = N, ry = N, rz = N;
-        if (k > 0) {  // k = 0: every offset is 0 and every remainder N
-            axis_entry(ax, N, k, qx, rx);
-            axis_entry(ay, N, k, qy, ry);
-            axis_entry(az, N, k, qz, rz);
-        }
-        const int32_t vx = x0 + (dx >= 0 ? qx : -qx);
-        const int32_t vy = y0 + (dy >= 0 ? qy : -qy);
-        const int32_t vz = z0 + (dz >= 0 ? qz : -qz);
-        P = static_cast<PackT>(vx) | (static_cast<PackT>(vy) * pack_unit<PackT>(1)) |
-            (static_cast<PackT>(vz) * pack_unit<PackT>(2));
-        L = static_cast<LinT>(vx) + static_cast<LinT>(vy) * w + static_cast<LinT>(vz) * wh;
         // major axis: the first with |d| = N; minors b, c are the other two in order
         const bool mx = (ax == N);
         const bool my = !mx && (ay == N);
@@ -203,10 +191,25 @@ struct Stepper {
         const int axis_m = mx ? 0 : (my ? 1 : 2);
         const int axis_b = mx ? 1 : 0;
         const int axis_c = (mx || my) ? 2 : 1;
+        // the major axis is at offset k (remainder N); one division per minor axis
+        int32_t qb = 0, qc = 0;
+        rb = N;
+        rc = N;
+        if (k > 0) {  // k = 0: every offset is 0 and every remainder N
+            axis_entry(abs(db), N, k, qb, rb);
+            axis_entry(abs(dc), N, k, qc, rc);
+        }
+        const int32_t qx = mx ? k : qb;
+        const int32_t qy = my ? k : (mx ? qb : qc);
+        const int32_t qz = (mx || my) ? qc : k;
+        const int32_t vx = x0 + (dx >= 0 ? qx : -qx);
+        const int32_t vy = y0 + (dy >= 0 ? qy : -qy);
+        const int32_t vz = z0 + (dz >= 0 ? qz : -qz);
+        P = static_cast<PackT>(vx) | (static_cast<PackT>(vy) * pack_unit<PackT>(1)) |
+            (static_cast<PackT>(vz) * pack_unit<PackT>(2));
+        L = static_cast<LinT>(vx) + static_cast<LinT>(vy) * w + static_cast<LinT>(vz) * wh;
         Ab2 = 2 * abs(db);
         Ac2 = 2 * abs(dc);
-        rb = mx ? ry : rx;
-        rc = (mx || my) ? rz : ry;
         dPm = signed_step<PackT>(dm, pack_unit<PackT>(axis_m));
         dPb = signed_step<PackT>(db, pack_unit<PackT>(axis_b));
         dPc = signed_step<PackT>(dc, pack_unit<PackT>(axis_c));
