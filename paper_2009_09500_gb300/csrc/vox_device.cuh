@@ -160,16 +160,26 @@ __device__ __forceinline__ T signed_step(int32_t d, T unit)
     return d > 0 ? unit : (d < 0 ? static_cast<T>(T(0) - unit) : T(0));
 }
 
+// x += y (mod 2^32); returns the carry out of bit 31 (0 or 1).
+__device__ __forceinline__ uint32_t add_carry(uint32_t &x, uint32_t y)
+{
+    uint32_t c;
+    asm("add.cc.u32 %0, %0, %2;\n\taddc.u32 %1, 0, 0;" : "+r"(x), "=r"(c) : "r"(y));
+    return c;
+}
+
 // Stepping state of one segment. PackT: uint32_t (LIST32) or uint64_t (LIST64);
 // LinT: uint32_t or uint64_t volume bit index (volumes up to or beyond 2^32 bits).
 // The three minor/major roles are fixed at entry: the major axis (|d| = N) moves
-// every step, the two minor axes move when their remainder reaches 2N.
+// every step, the two minor axes move when their remainder r (0 <= r < 2N) plus
+// 2|d| reaches 2N. Each r is held biased, as r + 2^32 - 2N (mod 2^32, no wrap for
+// r < 2N), so that adding 2|d| carries out of 32 bits exactly when the axis moves.
 template <typename PackT, typename LinT>
 struct Stepper {
-    int32_t left;     // steps still to take inside this segment after entry (N - k)
-    int32_t twoN;     // 2N
-    int32_t Ab2, Ac2; // 2|d| of the two minor axes
-    int32_t rb, rc;   // their remainders
+    int32_t left;        // steps still to take inside this segment after entry (N - k)
+    uint32_t Ab2, Ac2;   // 2|d| of the two minor axes
+    uint32_t eb, ec;     // their biased remainders
+    uint32_t bias;       // 2^32 - 2N (mod 2^32)
     PackT P, dPm, dPb, dPc;
     LinT L, dLm, dLb, dLc;
 
@@ -181,7 +191,6 @@ struct Stepper {
         const int32_t ax = abs(dx), ay = abs(dy), az = abs(dz);
         const int32_t N = max(ax, max(ay, az));
         left = N - k;
-        twoN = 2 * N;
         // major axis: the first with |d| = N; minors b, c are the other two in order
         const bool mx = (ax == N);
         const bool my = !mx && (ay == N);
@@ -192,9 +201,7 @@ struct Stepper {
         const int axis_b = mx ? 1 : 0;
         const int axis_c = (mx || my) ? 2 : 1;
         // the major axis is at offset k (remainder N); one division per minor axis
-        int32_t qb = 0, qc = 0;
-        rb = N;
-        rc = N;
+        int32_t qb = 0, qc = 0, rb = N, rc = N;
         if (k > 0) {  // k = 0: every offset is 0 and every remainder N
             axis_entry(abs(db), N, k, qb, rb);
             axis_entry(abs(dc), N, k, qc, rc);
@@ -208,8 +215,11 @@ struct Stepper {
         P = static_cast<PackT>(vx) | (static_cast<PackT>(vy) * pack_unit<PackT>(1)) |
             (static_cast<PackT>(vz) * pack_unit<PackT>(2));
         L = static_cast<LinT>(vx) + static_cast<LinT>(vy) * w + static_cast<LinT>(vz) * wh;
-        Ab2 = 2 * abs(db);
-        Ac2 = 2 * abs(dc);
+        Ab2 = 2u * static_cast<uint32_t>(abs(db));
+        Ac2 = 2u * static_cast<uint32_t>(abs(dc));
+        bias = 0u - 2u * static_cast<uint32_t>(N);
+        eb = static_cast<uint32_t>(rb) + bias;
+        ec = static_cast<uint32_t>(rc) + bias;
         dPm = signed_step<PackT>(dm, pack_unit<PackT>(axis_m));
         dPb = signed_step<PackT>(db, pack_unit<PackT>(axis_b));
         dPc = signed_step<PackT>(dc, pack_unit<PackT>(axis_c));
@@ -221,25 +231,21 @@ struct Stepper {
         dLc = signed_step<LinT>(dc, uc);
     }
 
-    // One step along the segment. Stepping past the last voxel is harmless (the
-    // state is simply not used again), so callers may step once too often.
+    // One step along the segment: the carries say which minor axes move, and a
+    // moved axis's remainder is re-biased (r + 2|d| - 2N). Stepping past the last
+    // voxel is harmless (the state is simply not used again), so callers may step
+    // once too often.
     template <bool kP, bool kL>
     __device__ __forceinline__ void step()
     {
         if (kP) P += dPm;
         if (kL) L += dLm;
-        rb += Ab2;
-        if (rb >= twoN) {
-            rb -= twoN;
-            if (kP) P += dPb;
-            if (kL) L += dLb;
-        }
-        rc += Ac2;
-        if (rc >= twoN) {
-            rc -= twoN;
-            if (kP) P += dPc;
-            if (kL) L += dLc;
-        }
+        const uint32_t cb = add_carry(eb, Ab2);
+        const uint32_t cc = add_carry(ec, Ac2);
+        eb += cb * bias;
+        ec += cc * bias;
+        if (kP) P += static_cast<PackT>(cb) * dPb + static_cast<PackT>(cc) * dPc;
+        if (kL) L += static_cast<LinT>(cb) * dLb + static_cast<LinT>(cc) * dLc;
     }
 };
 
