@@ -273,18 +273,20 @@ __device__ __forceinline__ int32_t euclid_steps(const int32_t *rec)
 }
 
 // Stepping state with the Euclidean N: no axis moves every step, so all three
-// carry (remainder r_a = (2 k A_a + N) mod 2N, the offset growing when it wraps).
+// carry (remainder r_a = (2 k A_a + N) mod 2N, the offset growing when it wraps;
+// A_a <= N since N = int(|d|) >= max |d_a|). As in Stepper, each r_a is held
+// biased by 2^32 - 2N, so that the carry of one add says whether the axis moves.
 template <typename PackT, typename LinT>
 struct EuclidStepper {
-    int32_t twoN;
-    int32_t A2[3], r[3];
+    uint32_t bias;         // 2^32 - 2N (mod 2^32)
+    uint32_t A2[3], e[3];  // 2 A_a and the biased remainders
     PackT P, dP[3];
     LinT L, dL[3];
 
     __device__ __forceinline__ void enter(const int32_t *rec, int32_t k, LinT w, LinT wh)
     {
         const int32_t N = euclid_steps(rec);
-        twoN = 2 * N;
+        bias = 0u - 2u * static_cast<uint32_t>(N);
         int32_t v[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -292,8 +294,8 @@ struct EuclidStepper {
             const int32_t A = abs(d);
             int32_t q = 0, rr = N;
             if (k > 0) axis_entry(A, N, k, q, rr);
-            r[a] = rr;
-            A2[a] = 2 * A;
+            e[a] = static_cast<uint32_t>(rr) + bias;
+            A2[a] = 2u * static_cast<uint32_t>(A);
             v[a] = rec[a] + (d >= 0 ? q : -q);
             dP[a] = signed_step<PackT>(d, pack_unit<PackT>(a));
             dL[a] = signed_step<LinT>(d, a == 0 ? LinT(1) : (a == 1 ? w : wh));
@@ -307,18 +309,15 @@ struct EuclidStepper {
     template <bool kP, bool kL>
     __device__ __forceinline__ bool step()
     {
-        bool moved = false;
+        uint32_t c[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            r[a] += A2[a];
-            if (r[a] >= twoN) {
-                r[a] -= twoN;
-                if (kP) P += dP[a];
-                if (kL) L += dL[a];
-                moved = true;
-            }
+            c[a] = add_carry(e[a], A2[a]);
+            e[a] += c[a] * bias;
         }
-        return moved;
+        if (kP) P += static_cast<PackT>(c[0]) * dP[0] + static_cast<PackT>(c[1]) * dP[1] + static_cast<PackT>(c[2]) * dP[2];
+        if (kL) L += static_cast<LinT>(c[0]) * dL[0] + static_cast<LinT>(c[1]) * dL[1] + static_cast<LinT>(c[2]) * dL[2];
+        return (c[0] | c[1] | c[2]) != 0u;
     }
 };
 
