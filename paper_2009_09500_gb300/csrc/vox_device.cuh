@@ -111,9 +111,16 @@ __device__ __forceinline__ void set_status(int32_t *status, int32_t code)
 }
 
 // ------------------------------------------------------- per-segment stepping
-// Voxel offset q and remainder r of one axis at step k (0 <= k <= N, N > 0):
-// q = floor((2 k A + N) / (2 N)), r = (2 k A + N) - 2 N q.
-__device__ __forceinline__ void axis_entry(int32_t A, int32_t N, int32_t k, int32_t &q, int32_t &r)
+// Voxel offset q and remainder r of one axis at step k (0 < k <= N < 2^22,
+// A <= N): q = floor((2 k A + N) / (2 N)), r = (2 k A + N) - 2 N q. rcp2N is
+// 1 / (2N) rounded to nearest in single precision. The quotient is estimated as
+// num * rcp2N in single precision: three roundings (num, the reciprocal, the
+// product), each of relative size at most 2^-24, keep the estimate within
+// 3 * 2^-24 * (A + 1/2) < 0.38 of num / (2N) for A < 2^21, so its integer part is
+// q - 1, q or q + 1, and the exact remainder (its value lies in (-4N, 4N), so it
+// is exact modulo 2^32) settles which: the estimate-and-correct step of long
+// division (Knuth, TAOCP vol. 2, 4.3.1), with one correction.
+__device__ __forceinline__ void axis_entry(int32_t A, int32_t N, int32_t k, float rcp2N, int32_t &q, int32_t &r)
 {
     if (A == N) {  // the numerator is N (mod 2N) for every k
         q = k;
@@ -121,18 +128,20 @@ __device__ __forceinline__ void axis_entry(int32_t A, int32_t N, int32_t k, int3
     } else if (A == 0) {
         q = 0;
         r = N;
-    } else if (N <= 46340) {  // 2 N^2 + N < 2^32: 32-bit unsigned division is exact
-        const uint32_t num = 2u * static_cast<uint32_t>(k) * static_cast<uint32_t>(A) + static_cast<uint32_t>(N);
-        const uint32_t den = 2u * static_cast<uint32_t>(N);
-        const uint32_t qq = num / den;
-        q = static_cast<int32_t>(qq);
-        r = static_cast<int32_t>(num - qq * den);
     } else {
+        const int32_t den = 2 * N;
         const uint64_t num = 2ull * static_cast<uint64_t>(k) * static_cast<uint64_t>(A) + static_cast<uint64_t>(N);
-        const uint64_t den = 2ull * static_cast<uint64_t>(N);
-        const uint64_t qq = num / den;
-        q = static_cast<int32_t>(qq);
-        r = static_cast<int32_t>(num - qq * den);
+        int32_t qq = __float2int_rz(__fmul_rn(__ull2float_rn(num), rcp2N));
+        int32_t rr = static_cast<int32_t>(static_cast<uint32_t>(num) - static_cast<uint32_t>(qq) * static_cast<uint32_t>(den));
+        if (rr < 0) {
+            --qq;
+            rr += den;
+        } else if (rr >= den) {
+            ++qq;
+            rr -= den;
+        }
+        q = qq;
+        r = rr;
     }
 }
 
@@ -203,8 +212,9 @@ struct Stepper {
         // the major axis is at offset k (remainder N); one division per minor axis
         int32_t qb = 0, qc = 0, rb = N, rc = N;
         if (k > 0) {  // k = 0: every offset is 0 and every remainder N
-            axis_entry(abs(db), N, k, qb, rb);
-            axis_entry(abs(dc), N, k, qc, rc);
+            const float rcp2N = __frcp_rn(static_cast<float>(2 * N));
+            axis_entry(abs(db), N, k, rcp2N, qb, rb);
+            axis_entry(abs(dc), N, k, rcp2N, qc, rc);
         }
         const int32_t qx = mx ? k : qb;
         const int32_t qy = my ? k : (mx ? qb : qc);
@@ -288,12 +298,13 @@ struct EuclidStepper {
         const int32_t N = euclid_steps(rec);
         bias = 0u - 2u * static_cast<uint32_t>(N);
         int32_t v[3];
+        const float rcp2N = k > 0 ? __frcp_rn(static_cast<float>(2 * N)) : 0.0f;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const int32_t d = rec[3 + a] - rec[a];
             const int32_t A = abs(d);
             int32_t q = 0, rr = N;
-            if (k > 0) axis_entry(A, N, k, q, rr);
+            if (k > 0) axis_entry(A, N, k, rcp2N, q, rr);
             e[a] = static_cast<uint32_t>(rr) + bias;
             A2[a] = 2u * static_cast<uint32_t>(A);
             v[a] = rec[a] + (d >= 0 ? q : -q);

@@ -233,6 +233,21 @@ def test_long_segments_wide_division():
     full_check(segs, dims, L64 | BM)
 
 
+def test_longest_near_diagonal_segments():
+    """N = 2^21 - 1 (the longest segment the packing allows) with minor |d| near N,
+    near N/2 and small: minor axes carry on almost every step and the biased
+    remainders reach the top of the 32-bit range; runs enter deep inside."""
+    M = (1 << 21) - 1
+    edge = 1 << 21
+    segs = np.array([
+        [0, 0, 0, M, M - 1, M - 2],
+        [M, 0, M, 0, M - 1, 1],
+        [0, M, 0, M, M // 2, M // 2 + 1],
+        [5, 7, M, M, 8, 3],
+    ], dtype=np.int32)
+    full_check(segs, (edge, edge, edge), L64)
+
+
 def test_volume_not_word_aligned():
     rng = np.random.default_rng(6)
     dims = (13, 7, 5)
