@@ -111,15 +111,32 @@ __device__ __forceinline__ void set_status(int32_t *status, int32_t code)
 }
 
 // ------------------------------------------------------- per-segment stepping
-// Voxel offset q and remainder r of one axis at step k (0 < k <= N < 2^22,
-// A <= N): q = floor((2 k A + N) / (2 N)), r = (2 k A + N) - 2 N q. rcp2N is
-// 1 / (2N) rounded to nearest in single precision. The quotient is estimated as
-// num * rcp2N in single precision: three roundings (num, the reciprocal, the
-// product), each of relative size at most 2^-24, keep the estimate within
-// 3 * 2^-24 * (A + 1/2) < 0.38 of num / (2N) for A < 2^21, so its integer part is
-// q - 1, q or q + 1, and the exact remainder (its value lies in (-4N, 4N), so it
-// is exact modulo 2^32) settles which: the estimate-and-correct step of long
+// q = floor(num / den) and r = num - q den for 1 <= den < 2^23 and num / den < 2^22,
+// given rcp = 1 / den rounded to nearest in single precision. The quotient is
+// estimated as num * rcp in single precision: three roundings (num, the
+// reciprocal, the product), each of relative size at most 2^-24, keep the
+// estimate within 3 * 2^-24 * 2^22 = 0.75 of num / den, so its integer part is
+// q - 1, q or q + 1, and the remainder of that guess (in (-2 den, 2 den), hence
+// exact modulo 2^32) settles which: the estimate-and-correct step of long
 // division (Knuth, TAOCP vol. 2, 4.3.1), with one correction.
+__device__ __forceinline__ void divmod_est(uint64_t num, int32_t den, float rcp, int32_t &q, int32_t &r)
+{
+    int32_t qq = __float2int_rz(__fmul_rn(__ull2float_rn(num), rcp));
+    int32_t rr = static_cast<int32_t>(static_cast<uint32_t>(num) - static_cast<uint32_t>(qq) * static_cast<uint32_t>(den));
+    if (rr < 0) {
+        --qq;
+        rr += den;
+    } else if (rr >= den) {
+        ++qq;
+        rr -= den;
+    }
+    q = qq;
+    r = rr;
+}
+
+// Voxel offset q and remainder r of one axis at step k (0 < k <= N < 2^22,
+// A <= N, A < 2^21): q = floor((2 k A + N) / (2 N)) <= A, r = (2 k A + N) - 2 N q.
+// rcp2N = 1 / (2N) rounded to nearest in single precision.
 __device__ __forceinline__ void axis_entry(int32_t A, int32_t N, int32_t k, float rcp2N, int32_t &q, int32_t &r)
 {
     if (A == N) {  // the numerator is N (mod 2N) for every k
@@ -129,19 +146,8 @@ __device__ __forceinline__ void axis_entry(int32_t A, int32_t N, int32_t k, floa
         q = 0;
         r = N;
     } else {
-        const int32_t den = 2 * N;
-        const uint64_t num = 2ull * static_cast<uint64_t>(k) * static_cast<uint64_t>(A) + static_cast<uint64_t>(N);
-        int32_t qq = __float2int_rz(__fmul_rn(__ull2float_rn(num), rcp2N));
-        int32_t rr = static_cast<int32_t>(static_cast<uint32_t>(num) - static_cast<uint32_t>(qq) * static_cast<uint32_t>(den));
-        if (rr < 0) {
-            --qq;
-            rr += den;
-        } else if (rr >= den) {
-            ++qq;
-            rr -= den;
-        }
-        q = qq;
-        r = rr;
+        divmod_est(2ull * static_cast<uint64_t>(k) * static_cast<uint64_t>(A) + static_cast<uint64_t>(N), 2 * N,
+                   rcp2N, q, r);
     }
 }
 

@@ -5,9 +5,10 @@ for each minor axis (Eq. (3)). The kernels estimate the quotient as
 num * rcp(2N) in single precision (round-to-nearest conversion, reciprocal and
 product) and correct the integer part once with the exact remainder taken modulo
 2^32. These tests check, on the host, that this estimate-and-correct sequence is
-exact over the whole domain the kernels use: 1 <= A < N, 1 <= k <= N, N up to
-int(|d|) of the longest Euclidean segment (sqrt(3) (2^21 - 1)). The GPU parity
-tests check the kernels' outputs themselves.
+exact over the domain it is written for (quotient below 2^22, divisor below
+2^23) and over the entry divisions with N up to int(|d|) of the longest
+Euclidean segment (sqrt(3) (2^21 - 1)). The GPU parity tests check the kernels'
+outputs themselves.
 """
 import numpy as np
 import pytest
@@ -30,6 +31,17 @@ def _check(N, A, k):
     q, r = estimate_and_correct(num, den)
     assert np.array_equal(q, num // den)
     assert np.array_equal(r, num % den)
+
+
+def test_generic_domain():
+    rng = np.random.default_rng(3)
+    m = 1 << 20
+    den = np.where(rng.random(m) < 0.5, rng.integers(1, 1 << 23, size=m), rng.integers(1, 5000, size=m))
+    q = np.where(rng.random(m) < 0.3, (1 << 22) - 1 - rng.integers(0, 100, size=m), rng.integers(0, 1 << 22, size=m))
+    r = np.where(rng.random(m) < 0.3, den - 1, rng.integers(0, den))
+    num = q * den + r
+    got_q, got_r = estimate_and_correct(num, den)
+    assert np.array_equal(got_q, q) and np.array_equal(got_r, r)
 
 
 def test_exhaustive_small_segments():
