@@ -301,7 +301,12 @@ struct EuclidStepper {
 
     __device__ __forceinline__ void enter(const int32_t *rec, int32_t k, LinT w, LinT wh)
     {
-        const int32_t N = euclid_steps(rec);
+        enter_n(rec, euclid_steps(rec), k, w, wh);
+    }
+
+    // As enter, with N = int(|E - S|) known (a segment's sample count minus one).
+    __device__ __forceinline__ void enter_n(const int32_t *rec, int32_t N, int32_t k, LinT w, LinT wh)
+    {
         bias = 0u - 2u * static_cast<uint32_t>(N);
         int32_t v[3];
         const float rcp2N = k > 0 ? __frcp_rn(static_cast<float>(2 * N)) : 0.0f;

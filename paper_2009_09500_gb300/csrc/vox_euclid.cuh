@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(256) k_euclid_runs(EuclidParams p)
             else hi = mid;
         }
         int64_t s = lo;
+        const int64_t seg_begin = __ldg(p.offsets + s);
         int64_t seg_end = __ldg(p.offsets + s + 1);
         int32_t rec[6];
         {
@@ -101,14 +102,15 @@ __global__ void __launch_bounds__(256) k_euclid_runs(EuclidParams p)
             }
         };
         prefetch(s);
-        const int32_t k0 = static_cast<int32_t>(g0 - __ldg(p.offsets + s));
+        // a segment's N is its sample count minus one (the scan counted N + 1)
+        const int32_t k0 = static_cast<int32_t>(g0 - seg_begin);
         EuclidStepper<PackT, LinT> st;
         bool add, first;
         if (k0 == 0) {
-            st.enter(rec, 0, w, wh);
+            st.enter_n(rec, static_cast<int32_t>(seg_end - seg_begin - 1), 0, w, wh);
             add = first = true;
         } else {  // sample k0 adds a voxel when some axis moved from sample k0 - 1
-            st.enter(rec, k0 - 1, w, wh);
+            st.enter_n(rec, static_cast<int32_t>(seg_end - seg_begin - 1), k0 - 1, w, wh);
             add = st.template step<kWrite && kList, kWrite && kMask>();
             first = false;
         }
@@ -116,13 +118,19 @@ __global__ void __launch_bounds__(256) k_euclid_runs(EuclidParams p)
         int32_t cnt = 0;
         LinT cur_word = static_cast<LinT>(~LinT(0));
         uint32_t acc = 0;
-        for (int64_t g = g0; g < g1; ++g) {
-            if (g == seg_end) {  // the next segment starts here
+        // samples g0 + i, i < n_i; the current segment ends before sample g0 + i_end
+        // (both below 2^31: a run is short and a segment has at most 2^22 samples)
+        const int32_t n_i = static_cast<int32_t>(g1 - g0);
+        int32_t i_end = static_cast<int32_t>(seg_end - g0);
+        for (int32_t i = 0; i < n_i; ++i) {
+            if (i == i_end) {  // the next segment starts here
                 ++s;
+                const int32_t N = static_cast<int32_t>(next_end - seg_end) - 1;
                 seg_end = next_end;
+                i_end = static_cast<int32_t>(seg_end - g0);
                 rec[0] = na.x; rec[1] = na.y; rec[2] = nb.x; rec[3] = nb.y; rec[4] = nc.x; rec[5] = nc.y;
                 prefetch(s);
-                st.enter(rec, 0, w, wh);
+                st.enter_n(rec, N, 0, w, wh);
                 add = first = true;
             }
             if (add) {
@@ -142,7 +150,7 @@ __global__ void __launch_bounds__(256) k_euclid_runs(EuclidParams p)
                 ++cnt;
             }
             first = false;
-            if (g + 1 < seg_end) add = st.template step<kWrite && kList, kWrite && kMask>();
+            if (i + 1 < i_end) add = st.template step<kWrite && kList, kWrite && kMask>();
         }
         if (kWrite && kMask && acc) red_or_keep(p.mask + cur_word, acc, keep_policy);
         if (!kWrite) p.run_count[j] = cnt;
@@ -154,8 +162,11 @@ __global__ void __launch_bounds__(256) k_euclid_runs(EuclidParams p)
 // samples, the last ones fewer), each lane appending its voxels to its own row
 // of a shared-memory stage; whenever a row fills, the warp flushes every row,
 // row by row, with coalesced stores at the rows' list positions. Segment offsets
-// and (optionally) the volume's atomics are written on the way.
-constexpr int kEuclidRow = 16;  // stage entries per lane
+// and (optionally) the volume's atomics are written on the way. Stage entries per
+// lane: 32 for 32-bit lists (one store instruction per row when it is full), 16
+// for 64-bit ones (the stage stays within 48 KB).
+template <typename PackT>
+__host__ __device__ constexpr int euclid_row() { return sizeof(PackT) == 4 ? 32 : 16; }
 
 template <int OUT, bool LIN64>
 __global__ void __launch_bounds__(256) k_euclid_list(EuclidParams p)
@@ -163,7 +174,8 @@ __global__ void __launch_bounds__(256) k_euclid_list(EuclidParams p)
     using PackT = typename std::conditional<(OUT & kOutList64) != 0, uint64_t, uint32_t>::type;
     using LinT = typename std::conditional<LIN64, uint64_t, uint32_t>::type;
     constexpr bool kMask = (OUT & kOutMask) != 0;
-    constexpr int kStride = kEuclidRow + 1;  // padded rows: lanes at equal fill hit different banks
+    constexpr int kRow = euclid_row<PackT>();
+    constexpr int kStride = kRow + 1;  // padded rows: lanes at equal fill hit different banks
     __shared__ PackT stage[8][32 * kStride];
     if (ld_volatile_i32(p.status) != 0) return;
     if (__ldg(p.run_off + p.n_runs) > p.capacity) {
@@ -200,18 +212,23 @@ __global__ void __launch_bounds__(256) k_euclid_list(EuclidParams p)
                 else hi = mid;
             }
             s = lo;
+            const int64_t seg_begin = __ldg(p.offsets + s);
             seg_end = __ldg(p.offsets + s + 1);
             load_record(p.segs, s, rec);
-            const int32_t k0 = static_cast<int32_t>(g0 - __ldg(p.offsets + s));
+            const int32_t N = static_cast<int32_t>(seg_end - seg_begin - 1);
+            const int32_t k0 = static_cast<int32_t>(g0 - seg_begin);
             if (k0 == 0) {
-                st.enter(rec, 0, w, wh);
+                st.enter_n(rec, N, 0, w, wh);
                 add = first = true;
             } else {
-                st.enter(rec, k0 - 1, w, wh);
+                st.enter_n(rec, N, k0 - 1, w, wh);
                 add = st.template step<true, kMask>();
             }
             outp = __ldg(p.run_off + j);
         }
+        // samples g0 + i, i < n_i (below 2^31, as in k_euclid_runs)
+        const int32_t n_i = static_cast<int32_t>(g1 - g0);
+        int32_t i_end = static_cast<int32_t>(seg_end - g0);
         int f = 0;
         LinT cur_word = static_cast<LinT>(~LinT(0));
         uint32_t acc = 0;
@@ -226,15 +243,18 @@ __global__ void __launch_bounds__(256) k_euclid_list(EuclidParams p)
             outp += f;
             f = 0;
         };
+        const int32_t n_it = static_cast<int32_t>(L);
 #pragma unroll 1
-        for (int64_t it = 0; it < L; ++it) {
-            const int64_t g = g0 + it;
-            if (g < g1) {
-                if (g == seg_end) {  // the next segment starts here
+        for (int32_t i = 0; i < n_it; ++i) {
+            if (i < n_i) {
+                if (i == i_end) {  // the next segment starts here
                     ++s;
-                    seg_end = __ldg(p.offsets + s + 1);
+                    const int64_t next_end = __ldg(p.offsets + s + 1);
+                    const int32_t N = static_cast<int32_t>(next_end - seg_end) - 1;
+                    seg_end = next_end;
+                    i_end = static_cast<int32_t>(seg_end - g0);
                     load_record(p.segs, s, rec);
-                    st.enter(rec, 0, w, wh);
+                    st.enter_n(rec, N, 0, w, wh);
                     add = first = true;
                 }
                 if (add) {
@@ -251,10 +271,10 @@ __global__ void __launch_bounds__(256) k_euclid_list(EuclidParams p)
                     }
                 }
                 first = false;
-                if (g + 1 < seg_end) add = st.template step<true, kMask>();
+                if (i + 1 < i_end) add = st.template step<true, kMask>();
             }
             __syncwarp();
-            if (__any_sync(0xffffffffu, f == kEuclidRow)) flush();
+            if (__any_sync(0xffffffffu, f == kRow)) flush();
         }
         __syncwarp();
         flush();
