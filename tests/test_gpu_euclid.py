@@ -114,8 +114,8 @@ def test_degenerate_and_axis_aligned():
 
 
 def test_long_segments_wide_entry():
-    """|E - S| up to about 3.6e6 (N above 46340: 64-bit entry division), runs that
-    start deep inside a segment."""
+    """|E - S| up to about 3.6e6 (N above 46340: entry numerators above 2^32), runs
+    that start deep inside a segment."""
     rng = np.random.default_rng(10)
     edge = 1 << 21
     segs = rng.integers(0, edge, size=(6, 6)).astype(np.int32)

@@ -2,7 +2,7 @@
 
 Bit-exact for every output (lists, volume words, counts, offsets): the method is
 integer-only, so the tolerance is zero. Sizes span several scan tiles (2048
-segments), several generation windows (1024 segments) and ragged tails; the
+segments), several generation windows (256 segments) and ragged tails; the
 full-size workloads run in the launch configuration that bench.py times.
 """
 
@@ -219,7 +219,7 @@ def test_ties_and_directions():
 
 
 def test_long_segments_wide_division():
-    """N above 46340 takes the 64-bit division when a run enters mid-segment."""
+    """N above 46340: entry numerators 2kA + N above 2^32 when a run enters mid-segment."""
     rng = np.random.default_rng(8)
     edge = 1 << 21
     dims = (edge, 16, 8)
