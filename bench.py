@@ -470,9 +470,10 @@ def run_ours(args):
     flags = vox.OUT_LIST32 | vox.OUT_BITMASK | vox.OUT_FRESH
     tuning = None
     if args.tuning:  # a given launch tuning (e.g. the one the tuner picks, for a profiler run)
-        r, vp, c = (int(x) for x in args.tuning.split(","))
-        vox.vox_set_tuning(r, vp, c)
-        tuning = {"params": {"run_len": r, "volume_path": vp, "ctas_per_sm": c}, "given": True}
+        knobs = [int(x) for x in args.tuning.split(",")] + [0]
+        r, vp, c, lr = knobs[:4]
+        vox.vox_set_tuning(r, vp, c, lr)
+        tuning = {"params": vox.vox_get_tuning(), "given": True}
     elif not args.no_tune:  # launch tuning for this GPU and workload class (outputs do not depend on it)
         from paper_2009_09500_gb300 import autotune
 
@@ -680,7 +681,8 @@ def run_ours(args):
     served = None
     if not args.no_serve and world == 1:
         served = measure_serving(args.serve_seconds, dev)
-    vox.vox_set_tuning(main_tuning["run_len"], main_tuning["volume_path"], main_tuning["ctas_per_sm"])
+    vox.vox_set_tuning(main_tuning["run_len"], main_tuning["volume_path"], main_tuning["ctas_per_sm"],
+                       main_tuning["list_runs"])
     sweeps = None
     if not args.no_sweeps and world == 1:
         sweeps = measure_sweeps(dev)
@@ -738,7 +740,7 @@ def main():
     ap.add_argument("--no-sweeps", action="store_true")
     ap.add_argument("--no-euclid", action="store_true")
     ap.add_argument("--no-bricked", action="store_true")
-    ap.add_argument("--tuning", default="", help="run_len,volume_path,ctas_per_sm: use this launch tuning")
+    ap.add_argument("--tuning", default="", help="run_len,volume_path,ctas_per_sm[,list_runs]: use this launch tuning")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()

@@ -416,6 +416,11 @@ vox_status vox_generate_noalloc(const vox_segment *d_segs, int64_t n, vox_dims d
  *                 VOX_VOLUME_ATOMIC (always per-voxel atomics)
  *   ctas_per_sm   persistent CTAs per SM for the generation and brick kernels
  *                 (0 = the occupancy maximum; larger values are capped there)
+ *   list_runs     32-bit list alone (no volume in the same launch): 0 = a
+ *                 thread's run of run_len voxels continues into the next
+ *                 segments (best when segments share one length that run_len
+ *                 divides or that divides run_len), 1 = runs end at segment ends
+ *                 (best for segments of varying length); other values are 0
  * vox_set_tuning(NULL) restores the defaults. Not to be changed while calls
  * are being issued from other host threads.
  */
@@ -425,7 +430,7 @@ typedef struct vox_tuning {
     int32_t run_len;
     int32_t volume_path;
     int32_t ctas_per_sm;
-    int32_t reserved;
+    int32_t list_runs;
 } vox_tuning;
 void vox_set_tuning(const vox_tuning *t);
 void vox_get_tuning(vox_tuning *t);

@@ -10,6 +10,7 @@ Tuned knobs (see include/vox.h, vox_tuning):
   run_len      voxels per thread run in the generation kernel (16, 32 or 64)
   volume_path  bricks when the workspace allows (auto) or per-voxel atomics
   ctas_per_sm  persistent CTAs per SM (0 = occupancy maximum, or fewer)
+  list_runs    32-bit list runs across segment ends (0) or cut at them (1)
 """
 
 from __future__ import annotations
@@ -21,11 +22,11 @@ import os
 from . import vox
 
 CANDIDATES = [
-    {"run_len": r, "volume_path": vp, "ctas_per_sm": c}
+    {"run_len": r, "volume_path": vp, "ctas_per_sm": c, "list_runs": 0}
     for r in (32, 64, 16)
     for vp in (vox.VOLUME_AUTO, vox.VOLUME_ATOMIC)
     for c in (0, 2)
-]
+] + [{"run_len": r, "volume_path": vox.VOLUME_AUTO, "ctas_per_sm": 0, "list_runs": 1} for r in (32, 64)]
 
 
 def default_cache_path() -> str:
@@ -60,7 +61,8 @@ def save_cache(cache: dict, path: str | None = None) -> None:
 
 
 def apply(params: dict) -> None:
-    vox.vox_set_tuning(params.get("run_len", 0), params.get("volume_path", 0), params.get("ctas_per_sm", 0))
+    vox.vox_set_tuning(params.get("run_len", 0), params.get("volume_path", 0), params.get("ctas_per_sm", 0),
+                       params.get("list_runs", 0))
 
 
 def measure(run, reps: int = 5, flush_bytes: int = 256 << 20) -> float:

@@ -341,6 +341,17 @@ vox_status launch_gen_t(const GenParams &p, cudaStream_t stream)
     if constexpr ((OUT & kOutList64) != 0) {
         if (current_tuning().run_len == 16) return launch_gen_r<16, OUT, LIN64>(p, stream);
         return launch_gen_r<32, OUT, LIN64>(p, stream);
+    } else if constexpr (OUT == kOutList32) {
+        // a 32-bit list alone may cut its runs at segment ends (list_runs = 1)
+        const vox_tuning tu = current_tuning();
+        if (tu.list_runs == 1 && p.scene_of == nullptr) {
+            if (tu.run_len == 16) return launch_gen_r<16, OUT | kOutSegRuns, LIN64>(p, stream);
+            if (tu.run_len == 64) return launch_gen_r<64, OUT | kOutSegRuns, LIN64>(p, stream);
+            return launch_gen_r<32, OUT | kOutSegRuns, LIN64>(p, stream);
+        }
+        if (tu.run_len == 16) return launch_gen_r<16, OUT, LIN64>(p, stream);
+        if (tu.run_len == 64) return launch_gen_r<64, OUT, LIN64>(p, stream);
+        return launch_gen_r<32, OUT, LIN64>(p, stream);
     } else {
         if (current_tuning().run_len == 16) return launch_gen_r<16, OUT, LIN64>(p, stream);
         if (current_tuning().run_len == 64) return launch_gen_r<64, OUT, LIN64>(p, stream);
@@ -1369,7 +1380,7 @@ void vox_set_tuning(const vox_tuning *t)
     if (g_tuning.run_len != 16 && g_tuning.run_len != 32 && g_tuning.run_len != 64) g_tuning.run_len = 0;
     if (g_tuning.volume_path < 0 || g_tuning.volume_path > VOX_VOLUME_ATOMIC) g_tuning.volume_path = 0;
     if (g_tuning.ctas_per_sm < 0) g_tuning.ctas_per_sm = 0;
-    g_tuning.reserved = 0;
+    if (g_tuning.list_runs != 1) g_tuning.list_runs = 0;
 }
 
 void vox_get_tuning(vox_tuning *t)

@@ -25,6 +25,7 @@
 namespace vox {
 
 __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+__device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
 
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
@@ -246,7 +247,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(ScanParams p)
 }
 
 // ------------------------------------------------------------------ generation
-enum : int { kOutList32 = 1, kOutList64 = 2, kOutMask = 4 };
+// kOutSegRuns: with kOutList32 alone, runs cut at segment ends (launch tuning list_runs)
+enum : int { kOutList32 = 1, kOutList64 = 2, kOutMask = 4, kOutSegRuns = 8 };
 
 struct GenParams {
     const int32_t *segs;     // [n][6], 16-byte aligned
@@ -267,19 +269,35 @@ struct GenParams {
     int32_t interleave;         // voxel tiles dealt round-robin to CTAs (else one range per CTA)
 };
 
+// Stage word of the pass's voxel at position x in the linear layout: two pad
+// words after every 2R positions, so that threads writing runs of R (or 2R)
+// voxels that start at multiples of R hit different banks (at most two-way), and
+// pairs (x even) never straddle a pad.
+template <int R>
+__host__ __device__ constexpr int32_t lin_index(int32_t x)
+{
+    return x + 2 * (x / (2 * R));
+}
+
 // Shared memory of k_generate: the staged window of segments and, for list
-// outputs, the pass's voxels in a transposed layout (run slot u of thread t at
-// u * S + t, S = 256 + 32 / R, or 257 for R >= 32) that is free of bank
-// conflicts when the threads write their runs and when the pass is read back
-// four voxels per thread (two-way for R = 64, where a warp reads 16 slots of
-// each of two threads).
+// outputs, the pass's voxels. Runs of R consecutive voxels that may cross into
+// the next segments use a transposed layout (run slot u of thread t at u * S + t,
+// S = 256 + 32 / R, or 257 for R >= 32) that is free of bank conflicts when the
+// threads write their runs and when the pass is read back four voxels per thread
+// (two-way for R = 64, where a warp reads 16 slots of each of two threads). A
+// 32-bit list alone with kOutSegRuns cuts its runs at segment ends instead,
+// staged linearly (lin_index).
 template <int R, int OUT>
 struct GenLayout {
     static constexpr bool kList = (OUT & (kOutList32 | kOutList64)) != 0;
     static constexpr bool kWide = (OUT & kOutList64) != 0;
+    static constexpr bool kSegRuns = OUT == (kOutList32 | kOutSegRuns);
     static constexpr int S = kGenThreads + (R >= 32 ? 1 : 32 / R);
     static constexpr int kPlanes = kWide ? 2 : 1;
-    static constexpr int kStageWords = kList ? kPlanes * R * S : 4;
+    // positions 0 .. kGenThreads R + 3 (a pass starts up to 3 after a multiple of 4), read in pairs
+    static constexpr int kLinWords = (lin_index<R>(kGenThreads * R + 3) + 2 + 3) & ~3;
+    static constexpr int kTransWords = kList ? kPlanes * R * S : 4;
+    static constexpr int kStageWords = kSegRuns ? kLinWords : kTransWords;
 };
 
 // The two TMA destinations (offs, recs) must start on 16-byte boundaries; they
@@ -289,6 +307,9 @@ struct GenSmem {
     alignas(16) int64_t offs[kWindowSegs + 2];
     alignas(16) int32_t recs[kWindowSegs * 6];
     alignas(16) uint32_t stage[GenLayout<R, OUT>::kStageWords];
+    int32_t runstart[kWindowSegs + 1];      // segment-cut runs: first run of each window segment
+    int32_t warp_tot[kGenThreads / 32];     // block scan
+    int64_t pass_lo, pass_hi;               // voxel range of the current pass
     uint64_t bar;
     int64_t V;
     int32_t go;
@@ -333,6 +354,45 @@ __device__ __forceinline__ int32_t find_in_window(const int64_t *offs, int32_t c
         if (m < cnt && offs[m] <= g) lo = m;
     }
     return lo;
+}
+
+// Largest j in [0, cnt) with rs[j] <= r (rs[0] = 0 <= r < rs[cnt]); the segment
+// found has at least one run, since a segment without runs shares its rs entry
+// with the next one.
+__device__ __forceinline__ int32_t find_run(const int32_t *rs, int32_t cnt, int32_t r)
+{
+    int32_t lo = 0;
+#pragma unroll
+    for (int32_t step = kWindowSegs / 2; step > 0; step >>= 1) {
+        const int32_t m = lo + step;
+        if (m < cnt && rs[m] <= r) lo = m;
+    }
+    return lo;
+}
+
+// Exclusive prefix sum of v over the CTA (kGenThreads threads, all calling);
+// total receives the sum. warp_tot: kGenThreads / 32 words of shared memory,
+// free until the caller's next barrier.
+__device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t *warp_tot, int32_t &total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    int32_t base = 0, tot = 0;
+#pragma unroll
+    for (int i = 0; i < kGenThreads / 32; ++i) {
+        const int32_t x = warp_tot[i];
+        base += i < wid ? x : 0;
+        tot += x;
+    }
+    total = tot;
+    return base + inc - v;
 }
 
 // OR `bits` into a volume word as a reduction (no return value), asking L2 to
@@ -436,6 +496,85 @@ __global__ void __launch_bounds__(kGenThreads, 3) k_generate(GenParams p)
         int64_t g_end = gB;
         if (win_end < gB) g_end = win_end & ~int64_t(3);
 
+        // runs cut at segment ends (kOutSegRuns): lanes of a warp do not wait on
+        // each other's segment changes when segment lengths differ; runs across
+        // segment ends (below) cost less when every lane changes segment at the
+        // same step (segments of one length that R divides, or that divides R)
+        if constexpr (L::kSegRuns) {
+            {
+                // the voxels of window segment j in [g0, g_end) form ceil(len / R)
+                // runs of R consecutive voxels (the last one shorter); thread t of a
+                // pass takes run r0 + t and enters its segment once
+                int32_t c = 0;
+                if (t < cnt) {
+                    const int64_t a = max64(sm.offs[t], g0), b = min64(sm.offs[t + 1], g_end);
+                    if (b > a) c = static_cast<int32_t>((b - a + R - 1) / R);
+                }
+                int32_t total_runs;
+                const int32_t first = block_exclusive_scan(c, sm.warp_tot, total_runs);
+                sm.runstart[t] = first;
+                if (t == kGenThreads - 1) sm.runstart[kGenThreads] = first + c;
+                __syncthreads();
+                for (int32_t r0 = 0; r0 < total_runs; r0 += kGenThreads) {
+                    const int32_t r = r0 + t;
+                    const int32_t n_runs = min(kGenThreads, total_runs - r0);
+                    int32_t j = 0, len = 0;
+                    int64_t g = 0;
+                    if (r < total_runs) {
+                        j = find_run(sm.runstart, cnt, r);
+                        g = max64(sm.offs[j], g0) + static_cast<int64_t>(r - sm.runstart[j]) * R;
+                        len = static_cast<int32_t>(min64(R, min64(sm.offs[j + 1], g_end) - g));
+                    }
+                    if (t == 0) sm.pass_lo = g;
+                    if (t == n_runs - 1) sm.pass_hi = g + len;
+                    __syncthreads();
+                    // stage position x holds voxel gb + x; gb is a multiple of 4, so
+                    // that 4-voxel groups and 16-byte aligned list addresses coincide
+                    const int64_t gb = sm.pass_lo & ~int64_t(3);
+                    const int32_t xs = static_cast<int32_t>(sm.pass_lo - gb);
+                    const int32_t xe = static_cast<int32_t>(sm.pass_hi - gb);
+                    if (r < total_runs) {
+                        Stepper<PackT, LinT> st;
+                        st.enter(sm.recs + 6 * j, static_cast<int32_t>(g - sm.offs[j]), w, wh);
+                        int32_t x = static_cast<int32_t>(g - gb);
+                        int32_t u = 0;
+                        for (; u < len && (x & 3) != 0; ++u, ++x) {  // up to a multiple of 4
+                            sm.stage[lin_index<R>(x)] = static_cast<uint32_t>(st.P);
+                            st.template step<true, false>();
+                        }
+                        // groups of four: one pointer, fixed offsets; a group never
+                        // straddles the pad after 2R positions
+                        uint32_t *sp = sm.stage + lin_index<R>(x);
+                        for (; u + 4 <= len; u += 4) {
+#pragma unroll
+                            for (int v = 0; v < 4; ++v) {
+                                sp[v] = static_cast<uint32_t>(st.P);
+                                st.template step<true, false>();
+                            }
+                            x += 4;
+                            sp += (x & (2 * R - 1)) == 0 ? 6 : 4;
+                        }
+                        for (; u < len; ++u, ++x) {
+                            sm.stage[lin_index<R>(x)] = static_cast<uint32_t>(st.P);
+                            st.template step<true, false>();
+                        }
+                    }
+                    __syncthreads();
+                    // write the pass out: voxels gb + [xs, xe), two per thread and
+                    // round (8-byte stores), the pass's first and last pair word by word
+                    for (int32_t x0 = 2 * t; x0 < xe; x0 += 2 * kGenThreads) {
+                        const uint2 v = *reinterpret_cast<const uint2 *>(sm.stage + lin_index<R>(x0));
+                        if (x0 >= xs && x0 + 2 <= xe) {
+                            *reinterpret_cast<uint2 *>(list + gb + x0) = v;
+                        } else {
+                            if (x0 >= xs) list[gb + x0] = v.x;
+                            if (x0 + 1 >= xs && x0 + 1 < xe) list[gb + x0 + 1] = v.y;
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+        } else
         // ---- passes over [g0, g_end): thread t takes the R consecutive voxels
         // starting at gp + t R, walking segment by segment
         for (int64_t gp = g0; gp < g_end; gp += kPass) {

@@ -53,7 +53,7 @@ VOLUME_ATOMIC = 1
 
 class Tuning(ctypes.Structure):
     _fields_ = [("run_len", ctypes.c_int32), ("volume_path", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("list_runs", ctypes.c_int32)]
 NOALLOC_MAX_SEGMENTS = 2000000
 
 
@@ -224,8 +224,8 @@ def vox_plan_batched(segs, scenes, n_scenes: int, total_bricks: int, ws, status,
     return int(v.value), int(pc.value)
 
 
-def vox_set_tuning(run_len: int = 0, volume_path: int = 0, ctas_per_sm: int = 0) -> None:
-    t = Tuning(int(run_len), int(volume_path), int(ctas_per_sm), 0)
+def vox_set_tuning(run_len: int = 0, volume_path: int = 0, ctas_per_sm: int = 0, list_runs: int = 0) -> None:
+    t = Tuning(int(run_len), int(volume_path), int(ctas_per_sm), int(list_runs))
     load().vox_set_tuning(ctypes.byref(t))
 
 
@@ -236,7 +236,7 @@ def vox_reset_tuning() -> None:
 def vox_get_tuning() -> dict:
     t = Tuning()
     load().vox_get_tuning(ctypes.byref(t))
-    return {"run_len": t.run_len, "volume_path": t.volume_path, "ctas_per_sm": t.ctas_per_sm}
+    return {"run_len": t.run_len, "volume_path": t.volume_path, "ctas_per_sm": t.ctas_per_sm, "list_runs": t.list_runs}
 
 
 def vox_mask_words(dims) -> int:
