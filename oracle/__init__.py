@@ -66,6 +66,8 @@ def load(path: str | None = None):
         getattr(lib, name).restype = i64
     lib.oracle_bitmask.argtypes = [p, i64, p, p, i64]
     lib.oracle_bitmask.restype = i64
+    lib.oracle_bitmask_zslab.argtypes = [p, i64, p, i64, i64, p, i64]
+    lib.oracle_bitmask_zslab.restype = i64
     lib.oracle_voxels_xyz.argtypes = [p, i64, i64, p, i64]
     lib.oracle_voxels_xyz.restype = i64
     lib.oracle_sectors_touched.argtypes = [p, i64]
@@ -168,6 +170,24 @@ class Oracle:
         got = self.lib.oracle_bitmask(self._ptr(a), a.shape[0], self._ptr(d), self._ptr(mask), mask.shape[0])
         assert got >= 0, "a voxel fell outside the volume"
         return mask
+
+    def slab_words(self, dims, z0: int, z1: int) -> int:
+        w, h, _ = (int(x) for x in dims)
+        return (w * h * (z1 - z0) + 31) // 32
+
+    def bitmask_zslab(self, segs, dims, z0: int, z1: int, slab: np.ndarray | None = None) -> np.ndarray:
+        """The volume's voxels with z in [z0, z1), OR-ed into a w x h x (z1 - z0)
+        slab (bit x + w (y + h (z - z0))); with z0 w h a multiple of 32 its words
+        are the whole volume's words from z0 w h / 32 on."""
+        a = self._segs(segs)
+        d = np.ascontiguousarray(dims, dtype=np.int32)
+        if slab is None:
+            slab = np.zeros(self.slab_words(dims, z0, z1), dtype=np.uint32)
+        assert slab.dtype == np.uint32 and slab.flags.c_contiguous
+        got = self.lib.oracle_bitmask_zslab(self._ptr(a), a.shape[0], self._ptr(d), int(z0), int(z1),
+                                            self._ptr(slab), slab.shape[0])
+        assert got >= 0, "a voxel fell outside the slab"
+        return slab
 
     def voxels_xyz(self, segs, s_begin: int = 0, s_end: int | None = None) -> np.ndarray:
         a = self._segs(segs)

@@ -196,6 +196,70 @@ int64_t oracle_bitmask(const int32_t *segs, int64_t n, const int32_t *dims, uint
     return outside ? -1 : g;
 }
 
+/* z of voxel k of a segment with N steps (Eq. (3), as oracle_voxel). */
+static int64_t voxel_z(const int32_t *seg, int64_t k, int64_t N)
+{
+    int64_t v[3];
+    voxel_of_sample(seg, k, N, v);
+    return v[2];
+}
+
+/* The smallest k in [0, N + 1] at which "z(k) >= zt" (rising: dz >= 0) or
+ * "z(k) < zt" (falling: dz < 0) holds, N + 1 if none: along a segment z moves
+ * monotonically from S_z to E_z (the rounding of Eq. (3) is monotone in k), so
+ * the predicate is false up to some k and true from there on, and bisection
+ * finds that k. */
+static int64_t first_step_past(const int32_t *seg, int64_t N, int64_t zt, int rising)
+{
+    int64_t lo = 0, hi = N + 1;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        int64_t z = voxel_z(seg, mid, N);
+        int holds = rising ? (z >= zt) : (z < zt);
+        if (holds)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
+/* The part of the occupancy volume with z in [z0, z1): the voxels of every
+ * segment with z0 <= z < z1 (Eq. (3), as oracle_bitmask) OR-ed into `slab`, a
+ * volume of w x h x (z1 - z0) voxels whose bit index is x + w * (y + h * (z - z0)).
+ * When z0 * w * h is a multiple of 32, slab word j is word j + z0 * w * h / 32 of
+ * the whole volume, so a large volume can be checked slab by slab. The voxels of
+ * a segment inside the slab are those of one range of k (z is monotone in k),
+ * found by bisection; each is still tested against the slab. Returns the number
+ * of voxels OR-ed in, or -1 if the slab has fewer than n_words words for them. */
+int64_t oracle_bitmask_zslab(const int32_t *segs, int64_t n, const int32_t *dims, int64_t z0, int64_t z1,
+                             uint32_t *slab, int64_t n_words)
+{
+    const int64_t w = dims[0];
+    const int64_t h = dims[1];
+    int64_t in_slab = 0;
+    int outside = 0;
+    for (int64_t s = 0; s < n; ++s) {
+        const int32_t *seg = segs + 6 * s;
+        int64_t N = oracle_steps(seg);
+        int rising = seg[5] >= seg[2];
+        int64_t kb = first_step_past(seg, N, rising ? z0 : z1, rising);
+        int64_t ke = first_step_past(seg, N, rising ? z1 : z0, rising);
+        for (int64_t k = kb; k < ke; ++k) {
+            int64_t v[3];
+            oracle_voxel(seg, k, v);
+            if (v[2] < z0 || v[2] >= z1) continue;
+            uint64_t bit = (uint64_t)(v[0] + w * v[1] + w * h * (v[2] - z0));
+            if (bit / 32 < (uint64_t)n_words)
+                slab[bit / 32] |= (uint32_t)1 << (bit % 32);
+            else
+                outside = 1;
+            ++in_slab;
+        }
+    }
+    return outside ? -1 : in_slab;
+}
+
 /* Voxels of segments [s_begin, s_end) only, written as x, y, z triples; at most
  * `cap` voxels are written, the return value is the number produced. */
 int64_t oracle_voxels_xyz(const int32_t *segs, int64_t s_begin, int64_t s_end, int64_t *xyz,

@@ -323,6 +323,25 @@ def pin_outputs_agree(O, segs, dims):
     assert np.array_equal(m2, m)
 
 
+def pin_zslab(O, segs, dims, cuts):
+    """A z-slab [z0, z1) of the volume holds exactly the voxels of the voxel
+    sequence with z0 <= z < z1, at bit x + w (y + h (z - z0)), and nothing else;
+    the slabs between consecutive `cuts` together hold every voxel once."""
+    segs = np.asarray(segs, dtype=np.int32)
+    w, h, _ = (int(v) for v in dims)
+    xyz = O.voxels_xyz(segs)
+    covered = 0
+    for z0, z1 in zip(cuts[:-1], cuts[1:]):
+        sel = (xyz[:, 2] >= z0) & (xyz[:, 2] < z1)
+        want = np.unique(xyz[sel, 0] + w * (xyz[sel, 1] + h * (xyz[sel, 2] - z0)))
+        slab = O.bitmask_zslab(segs, dims, z0, z1)
+        assert slab.shape[0] == (w * h * (z1 - z0) + 31) // 32
+        got = np.flatnonzero(np.unpackbits(slab.view(np.uint8), bitorder="little"))
+        assert np.array_equal(got, want), (z0, z1)
+        covered += int(sel.sum())
+    assert covered == len(xyz)
+
+
 # ------------------------------------------------------------------ validation
 def pin_validate(O):
     ok = np.array([[0, 0, 0, 9, 9, 9]], dtype=np.int32)

@@ -104,6 +104,33 @@ def test_outputs_agree_odd_volume(orc):
     P.pin_outputs_agree(orc, segs, dims)
 
 
+def test_zslab_config1(orc):
+    """Slabs of the 256^3 volume, cut at word-aligned and ragged planes, with
+    segments crossing the cuts."""
+    w = workloads.config1()
+    P.pin_zslab(orc, w.segs[:600], w.dims, [0, 1, 37, 64, 128, 129, 255, 256])
+
+
+def test_zslab_odd_volume(orc):
+    rng = np.random.default_rng(17)
+    dims = (13, 7, 21)
+    segs = workloads.uniform_segments(rng, 400, dims)
+    P.pin_zslab(orc, segs, dims, [0, 3, 4, 10, 20, 21])
+    # an empty slab
+    assert not orc.bitmask_zslab(segs, dims, 5, 5).any()
+
+
+def test_zslab_words_align_with_the_whole_volume(orc):
+    """With z0 w h a multiple of 32 the slab's words are the volume's words."""
+    rng = np.random.default_rng(18)
+    dims = (64, 16, 48)
+    segs = workloads.uniform_segments(rng, 500, dims)
+    full = orc.bitmask(segs, dims)
+    per_plane = 64 * 16 // 32
+    for z0, z1 in ((0, 16), (16, 40), (40, 48)):
+        assert np.array_equal(orc.bitmask_zslab(segs, dims, z0, z1), full[z0 * per_plane:z1 * per_plane])
+
+
 def test_generator_shapes():
     w2 = workloads.config2(n_fixed=4096)
     d = (w2.segs[:, 3:].astype(np.int64) - w2.segs[:, :3])

@@ -46,6 +46,9 @@ MUTANTS = [
     ("repeat test on x only", "if (k > 0 && v[0] == prev[0] && v[1] == prev[1] && v[2] == prev[2]) continue;",
      "if (k > 0 && v[0] == prev[0]) continue;"),
     ("variant uses N = max|d|", "    return oracle_isqrt(sq);", "    return oracle_steps(seg);"),
+    ("slab offset dropped", "w * h * (v[2] - z0)", "w * h * v[2]"),
+    ("slab search off by one", "            lo = mid + 1;", "            lo = mid + 1 + (mid == 0);"),
+    ("slab search ignores the direction", "int rising = seg[5] >= seg[2];", "int rising = 1;"),
 ]
 
 
@@ -67,6 +70,8 @@ def _pins(O):
         ("euclid_isqrt", lambda: P.pin_euclid_isqrt(O)),
         ("euclid_brute_force", lambda: P.pin_euclid_brute_force(O, P.all_pairs(3))),
         ("euclid_invariants", lambda: P.pin_euclid_invariants(O, workloads.config1().segs[:100])),
+        ("zslab", lambda: P.pin_zslab(O, workloads.uniform_segments(rng, 200, (40, 12, 24)), (40, 12, 24),
+                                      [0, 5, 6, 13, 24])),
     ]
     for name, fn in checks:
         try:
