@@ -114,11 +114,12 @@ def get_oracle():
     return oracle.get()
 
 
-def brick_pieces_expected(O, segs, dims):
-    """Number of brick pieces (maximal runs of a segment's voxels inside one
-    brick) from the oracle's voxels and the documented brick shape: B0 = the
-    largest 32 * 2^k not above min(w, 256), then the largest power-of-two rows
-    B1 x B2 (B1 = 2 B2 or B2) with B0/32 * B1 * B2 <= 32768 words."""
+def brick_pieces_expected(O, segs, dims, max_len=64):
+    """Number of brick pieces from the oracle's voxels and the documented brick
+    shape: every maximal run of a segment's voxels inside one brick, cut into
+    parts of at most max_len voxels. Brick shape: B0 = the largest 32 * 2^k not
+    above min(w, 256), then the largest power-of-two rows B1 x B2 (B1 = 2 B2 or
+    B2) with B0/32 * B1 * B2 <= 32768 words."""
     w = int(dims[0])
     b0 = 32
     while 2 * b0 <= min(w, 256):
@@ -134,8 +135,10 @@ def brick_pieces_expected(O, segs, dims):
     starts = np.zeros(len(xyz), dtype=bool)
     starts[np.concatenate([[0], np.cumsum(counts)[:-1]])] = True
     bc = xyz // B
-    change = np.any(bc[1:] != bc[:-1], axis=1) & ~starts[1:]
-    return int(starts.sum() + change.sum())
+    first = starts.copy()
+    first[1:] |= np.any(bc[1:] != bc[:-1], axis=1)
+    runs = np.diff(np.concatenate([np.flatnonzero(first), [len(xyz)]]))
+    return int(((runs + max_len - 1) // max_len).sum())
 
 
 def bricked_from_row_major(mask_u32: np.ndarray, dims) -> np.ndarray:

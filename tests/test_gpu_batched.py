@@ -76,16 +76,6 @@ def test_batched_with_empty_and_odd_scenes():
     check_scenes(b, scenes)
 
 
-def test_batched_config4_full_size_sampled():
-    """The 256-scene batch: scene bases in full, 24 scenes compared in full."""
-    scenes = workloads.config4()
-    b = batching.make_batch(scenes)
-    b.run()
-    rng = np.random.default_rng(7)
-    sample = sorted(set([0, len(scenes) - 1] + list(rng.choice(len(scenes), 22, replace=False))))
-    check_scenes(b, scenes, sample)
-
-
 def test_batched_equals_plain_and_graph_replay():
     scenes = small_scenes(32, seed=43)
     b = batching.make_batch(scenes)
@@ -259,3 +249,17 @@ def test_batched_bricks_wrong_total_is_refused_on_the_device():
     b.run()
     torch.cuda.synchronize()
     assert int(b.status.item()) == vox.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("volume_path", [vox.VOLUME_ATOMIC, vox.VOLUME_ATOMIC_WARP])
+def test_batched_atomic_volume_paths(volume_path):
+    """The batched volumes by per-voxel atomics (per-lane merging, and merged
+    across the warp), every scene against the oracle."""
+    scenes = small_scenes(20, seed=47)
+    b = batching.make_batch(scenes, flags=vox.OUT_BITMASK)
+    try:
+        vox.vox_set_tuning(32, volume_path, 0)
+        b.run()
+        check_scenes(b, scenes)
+    finally:
+        vox.vox_reset_tuning()

@@ -92,80 +92,6 @@ def test_config3_prefix_list64_and_sparse_mask():
     check_mask_sparse(mask, words, bits)
 
 
-def test_config3_full_size_sampled():
-    """All 4M segments (V ~ 2.07e9) with the 64-bit list (16.5 GB) and the
-    8 GiB volume: counts and offsets compared in full, 3000 sampled segments'
-    voxels compared in the list and found set in the volume."""
-    w = workloads.config3()
-    O = get_oracle()
-    segs = torch.from_numpy(w.segs).cuda()
-    n = segs.shape[0]
-    ws = torch.empty(vox.vox_workspace_size(n), dtype=torch.uint8, device="cuda")
-    status = torch.zeros(1, dtype=torch.int32, device="cuda")
-    counts = O.count(w.segs)
-    off = O.offsets(counts)
-    V = int(off[-1])
-    assert V > 2_000_000_000 and 8 * V > (1 << 33)  # list byte offsets beyond 33 bits
-    d_off = torch.empty(n + 1, dtype=torch.int64, device="cuda")
-    vox.vox_count(segs, w.dims, ws, status, None, d_off)
-    torch.cuda.synchronize()
-    assert int(status.item()) == 0
-    assert np.array_equal(d_off.cpu().numpy(), off)
-    lst = torch.empty(V, dtype=torch.int64, device="cuda")
-    mask = torch.zeros(vox.vox_mask_words(w.dims), dtype=torch.int32, device="cuda")
-    vox.vox_generate(segs, w.dims, ws, status, lst, mask)
-    torch.cuda.synchronize()
-    assert int(status.item()) == 0
-    rng = np.random.default_rng(99)
-    sample = np.unique(np.concatenate([rng.integers(0, n, size=3000), [0, n - 1]]))
-    wdim, hdim = w.dims[0], w.dims[1]
-    for chunk in np.array_split(sample, 10):
-        idx = np.concatenate([np.arange(off[s], off[s + 1]) for s in chunk])
-        got = lst[torch.from_numpy(idx).cuda()].cpu().numpy().view(np.uint64)
-        want = np.concatenate([O.list64(w.segs[s:s + 1]) for s in chunk])
-        assert np.array_equal(got, want)
-        words, bits = sparse_mask_from_list64(want, w.dims)
-        m = mask[torch.from_numpy(words).cuda()].cpu().numpy().view(np.uint32)
-        assert ((m & bits) == bits).all(), "a sampled voxel is missing from the volume"
-    del lst, mask
-    torch.cuda.empty_cache()
-
-
-def test_total_beyond_2_to_31_sampled():
-    """1.1M segments of 2000 voxels in the 4096^3 volume: V = 2.2e9 > 2^31, so the
-    scan totals, offsets and voxel ids need 64 bits. Offsets compared in full,
-    sampled segments compared in the 64-bit list and the volume."""
-    rng = np.random.default_rng(31)
-    n = 1_100_000
-    segs = workloads._segments_from_major(rng, np.full(n, 1999, np.int64), 4096)
-    dims = (4096, 4096, 4096)
-    O = get_oracle()
-    off = O.offsets(O.count(segs))
-    V = int(off[-1])
-    assert V == n * 2000 and V > (1 << 31)
-    d_segs = torch.from_numpy(segs).cuda()
-    ws = torch.empty(vox.vox_workspace_size(n), dtype=torch.uint8, device="cuda")
-    status = torch.zeros(1, dtype=torch.int32, device="cuda")
-    d_off = torch.empty(n + 1, dtype=torch.int64, device="cuda")
-    vox.vox_count(d_segs, dims, ws, status, None, d_off)
-    lst = torch.empty(V, dtype=torch.int64, device="cuda")
-    mask = torch.zeros(vox.vox_mask_words(dims), dtype=torch.int32, device="cuda")
-    vox.vox_generate(d_segs, dims, ws, status, lst, mask)
-    torch.cuda.synchronize()
-    assert int(status.item()) == 0
-    assert np.array_equal(d_off.cpu().numpy(), off)
-    sample = np.unique(np.concatenate([rng.integers(0, n, size=400), [0, n // 2, n - 1]]))
-    idx = np.concatenate([np.arange(off[s], off[s + 1]) for s in sample])
-    got = lst[torch.from_numpy(idx).cuda()].cpu().numpy().view(np.uint64)
-    want = np.concatenate([O.list64(segs[s:s + 1]) for s in sample])
-    assert np.array_equal(got, want)
-    words, bits = sparse_mask_from_list64(want, dims)
-    m = mask[torch.from_numpy(words).cuda()].cpu().numpy().view(np.uint32)
-    assert ((m & bits) == bits).all()
-    del lst, mask
-    torch.cuda.empty_cache()
-
-
 # --------------------------------------------------------------------- edge cases
 def test_empty_input():
     r = run_gpu(np.zeros((0, 6), np.int32), (8, 8, 8), L32 | BM)
@@ -457,39 +383,6 @@ def test_bricks_config3_prefix_sparse():
     check_mask_sparse(mask, words, bits)
 
 
-def test_bricks_config3_full_size_sampled():
-    """All 4M log-uniform segments, 8 GiB volume built by bricks: sampled
-    segments' voxels must be set, and the set-bit count must equal the atomic
-    path's on the same input."""
-    w = workloads.config3()
-    O = get_oracle()
-    segs = torch.from_numpy(w.segs).cuda()
-    n = w.n
-    status = torch.zeros(1, dtype=torch.int32, device="cuda")
-    ws = torch.empty(vox.vox_workspace_size_volume(n, w.dims, 0), dtype=torch.uint8, device="cuda")
-    V, P = vox.vox_plan(segs, w.dims, ws, status)
-    ws = torch.empty(vox.vox_workspace_size_volume(n, w.dims, P), dtype=torch.uint8, device="cuda")
-    mask = torch.zeros(vox.vox_mask_words(w.dims), dtype=torch.int32, device="cuda")
-    vox.vox_generate(segs, w.dims, ws, status, None, mask)
-    torch.cuda.synchronize()
-    assert int(status.item()) == 0
-    rng = np.random.default_rng(98)
-    sample = rng.integers(0, n, size=2000)
-    want = np.concatenate([O.list64(w.segs[s:s + 1]) for s in sample])
-    words, bits = sparse_mask_from_list64(want, w.dims)
-    m = mask[torch.from_numpy(words).cuda()].cpu().numpy().view(np.uint32)
-    assert ((m & bits) == bits).all()
-    del ws
-    ws2 = torch.empty(vox.vox_workspace_size(n), dtype=torch.uint8, device="cuda")
-    mask2 = torch.zeros_like(mask)
-    vox.vox_generate(segs, w.dims, ws2, status, None, mask2)
-    torch.cuda.synchronize()
-    assert int(status.item()) == 0
-    assert torch.equal(mask, mask2), "brick and atomic volumes differ"
-    del mask, mask2
-    torch.cuda.empty_cache()
-
-
 def test_bricks_generation_repeated_after_one_count():
     """vox_count once, then the volume pass twice (fresh volumes): both exact.
     The brick pass resets its own tickets, so it can run again on the counts."""
@@ -647,3 +540,49 @@ def test_bricked_errors_and_empty():
     r = run_gpu(np.zeros((0, 6), np.int32), dims, BM | BR, mask_words=words,
                 mask_init=np.full(words, 0xFFFFFFFF, np.uint32), pieces=1)
     assert r["status"] == 0 and (r["mask"] == 0).all()
+
+
+# ------------------------------------- per-voxel atomics merged across the warp
+@pytest.mark.parametrize("dims,n,mode", [
+    ((256, 256, 256), 4096, "zero"),   # the 4096-segment workload's shape
+    ((13, 7, 5), 3000, "zero"),        # rows not word aligned, words shared by many lanes
+    ((64, 64, 64), 20000, "or"),       # dense: lanes often hold equal words; OR into stale bits
+    ((1024, 16, 8), 500, "zero"),      # long flat segments: runs that cross segment ends
+])
+def test_warp_merged_atomics(dims, n, mode):
+    """The volume alone by per-voxel atomics merged across the warp
+    (VOX_VOLUME_ATOMIC_WARP), against the oracle, for every run length."""
+    rng = np.random.default_rng(sum(dims) + n)
+    segs = workloads.uniform_segments(rng, n, dims)
+    init = None
+    if mode == "or":
+        init = rng.integers(0, 2**32, size=vox.vox_mask_words(dims), dtype=np.uint64).astype(np.uint32)
+        init[::2] = 0
+    try:
+        for r in (16, 32, 64):
+            vox.vox_set_tuning(r, vox.VOLUME_ATOMIC_WARP, 0)
+            full_check(segs, dims, BM, pieces="plan", mask_init=None if init is None else init.copy())
+            full_check(segs, dims, BM | FR, pieces="plan", mask_init=garbage_mask(rng, dims))
+    finally:
+        vox.vox_reset_tuning()
+
+
+def test_warp_merged_atomics_config3_prefix():
+    """64-bit bit indices (4096^3 volume), long segments: the sparse volume."""
+    w = workloads.config3(n=60000)
+    O = get_oracle()
+    segs = torch.from_numpy(w.segs).cuda()
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ws = torch.empty(vox.vox_workspace_size(w.n), dtype=torch.uint8, device="cuda")
+    mask = torch.zeros(vox.vox_mask_words(w.dims), dtype=torch.int32, device="cuda")
+    try:
+        vox.vox_set_tuning(32, vox.VOLUME_ATOMIC_WARP, 0)
+        vox.vox_generate(segs, w.dims, ws, status, None, mask)
+        torch.cuda.synchronize()
+    finally:
+        vox.vox_reset_tuning()
+    assert int(status.item()) == 0
+    words, bits = sparse_mask_from_list64(O.list64(w.segs), w.dims)
+    check_mask_sparse(mask, words, bits)
+    del mask
+    torch.cuda.empty_cache()
