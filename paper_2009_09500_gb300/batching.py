@@ -87,17 +87,15 @@ class Batch:
 
 def make_batch(workloads_list, flags=vox.OUT_LIST32 | vox.OUT_BITMASK, device="cuda", bricks=True) -> Batch:
     """Upload scenes (workloads.Workload objects) as one batch. The list is sized
-    exactly (from the segments' voxel counts, summed here on the host from the
-    same input bytes; the device recounts and checks the capacity). With
-    ``bricks`` (and every scene's width a multiple of 32) the volumes are built
-    by bricks, the workspace sized by vox_plan_batched."""
+    exactly by the device's plan of the batch (vox_plan_batched: the scan's
+    voxel total and, with ``bricks`` and every scene's width a multiple of 32,
+    the brick pieces that size the workspace); the launch recounts and checks
+    the capacity."""
     import torch
 
     segs_np = np.ascontiguousarray(np.concatenate([w.segs for w in workloads_list], axis=0), dtype=np.int32)
     seg_counts = [w.n for w in workloads_list]
     dims = [tuple(w.dims) for w in workloads_list]
-    d = np.abs(segs_np[:, 3:].astype(np.int64) - segs_np[:, :3])
-    V = int((d.max(axis=1) + 1).sum()) if len(segs_np) else 0
     masks = []
     if flags & vox.OUT_BITMASK:  # fresh volumes are cleared by the launch itself
         alloc = torch.empty if flags & vox.OUT_FRESH else torch.zeros
@@ -105,26 +103,25 @@ def make_batch(workloads_list, flags=vox.OUT_LIST32 | vox.OUT_BITMASK, device="c
     ptrs = [m.data_ptr() for m in masks] if masks else [0] * len(dims)
     table = scene_table_bytes(seg_counts, dims, ptrs)
     scenes = torch.frombuffer(bytearray(table), dtype=torch.uint8).to(device)
-    lst = None
-    if flags & vox.OUT_LIST64:
-        lst = torch.empty(max(V, 1), dtype=torch.int64, device=device)
-    elif flags & vox.OUT_LIST32:
-        lst = torch.empty(max(V, 1), dtype=torch.int32, device=device)
     n_scenes = len(workloads_list)
     d_segs = torch.from_numpy(segs_np).to(device)
     status = torch.zeros(1, dtype=torch.int32, device=device)
     per_scene = [vox.vox_scene_bricks(dm) for dm in dims]
     total_bricks = sum(per_scene) if (bricks and flags & vox.OUT_BITMASK and len(segs_np) and
                                       all(b > 0 for b in per_scene)) else 0
-    pieces = 0
+    ws = torch.empty(vox.vox_workspace_size_batched_volume(len(segs_np), n_scenes, total_bricks, 0),
+                     dtype=torch.uint8, device=device)
+    V, pieces = vox.vox_plan_batched(d_segs, scenes, n_scenes, total_bricks, ws, status)
     if total_bricks:
-        ws = torch.empty(vox.vox_workspace_size_batched_volume(len(segs_np), n_scenes, total_bricks, 0),
-                         dtype=torch.uint8, device=device)
-        _, pieces = vox.vox_plan_batched(d_segs, scenes, n_scenes, total_bricks, ws, status)
         size = vox.vox_workspace_size_batched_volume(len(segs_np), n_scenes, total_bricks, pieces)
     else:
         size = vox.vox_workspace_size_batched(len(segs_np), n_scenes)
     ws = torch.empty(size, dtype=torch.uint8, device=device)
+    lst = None
+    if flags & vox.OUT_LIST64:
+        lst = torch.empty(max(V, 1), dtype=torch.int64, device=device)
+    elif flags & vox.OUT_LIST32:
+        lst = torch.empty(max(V, 1), dtype=torch.int32, device=device)
     return Batch(segs=d_segs, scenes=scenes, n_scenes=n_scenes, dims=dims, seg_counts=seg_counts, masks=masks,
                  lst=lst, scene_base=torch.zeros(n_scenes + 1, dtype=torch.int64, device=device), ws=ws,
                  status=status, flags=flags, V=V, total_bricks=total_bricks, pieces=pieces)

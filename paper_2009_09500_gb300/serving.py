@@ -3,16 +3,20 @@
 Each request is a scene (segments + volume extent) whose result is an occupancy
 volume kept resident on the device. Requests arrive over time (a Poisson stream
 in the benchmark); the loop admits them first-come first-served while their
-device bytes fit a memory budget and an in-flight slot is free, packs the
-admitted requests into one batch, and launches the batch with
-vox_generate_batched on one of several streams. Batches launched while earlier
+device bytes fit the free device memory (a live probe, under an optional cap)
+and an in-flight slot is free, packs the admitted requests into one batch, and
+launches the batch with vox_generate_batched on one of several streams. Batches launched while earlier
 ones still run overlap on the device, and requests that arrive meanwhile join
 the next batch as slots and memory free up (continuous batching). Latency is
 completion minus arrival, on the host clock.
 
 The scheduler (admission, slots, bookkeeping) is plain Python and takes its
 launcher, memory probe and clock as arguments, so that it can be exercised on
-the CPU with fakes; the default launcher runs libvox on the GPU.
+the CPU with fakes; the default launcher runs libvox on the GPU, and the
+default probe (gpu_free_bytes) reads the device's free memory. A request's
+voxel count, used for the throughput figure, comes back from the device with
+its batch (the scan's per-scene voxel bases); the host does none of the
+method's arithmetic.
 """
 
 from __future__ import annotations
@@ -32,7 +36,7 @@ class ServeRequest:
     n: int
     dims: tuple
     segs_host: object = None      # pinned CPU int32 [n, 6] tensor (default launcher)
-    voxels: int = 0               # total voxels (for throughput accounting)
+    voxels: int = 0               # total voxels, reported by the device with the batch
     admitted_s: float = math.nan
     done_s: float = math.nan
     status: int = -1
@@ -46,10 +50,12 @@ class ServeRequest:
 
     @property
     def piece_capacity(self) -> int:
-        """Room for brick pieces: a segment of L voxels has at most about 1 + 2L/64
-        pieces in 256 x 64 x 64 bricks; twice that covers random directions, and
-        pieces beyond it fall back to atomics on the device."""
-        return 2 * self.n + self.voxels // 16 + 1024
+        """Room for brick pieces, from the request's size alone: a segment of a
+        volume of edge E crosses at most about E/64 brick faces per axis in
+        256 x 64 x 64 bricks (fewer with the uniform endpoints served here), so
+        2 + E/32 pieces per segment is ample; pieces beyond the room fall back
+        to per-voxel atomics on the device, with the same result."""
+        return self.n * (2 + max(self.dims) // 32) + 1024
 
     @property
     def device_bytes(self) -> int:
@@ -63,24 +69,38 @@ class ServeRequest:
 
 class Admission:
     """First-come first-served admission: take requests from the head of the
-    queue while they fit the free-byte budget and the batch limits; a request
-    larger than the whole budget can never run and is rejected."""
+    queue while they fit the free device memory and the batch limits. With a
+    memory probe (free bytes now, the in-flight batches' memory already taken)
+    a request is admitted while it fits the probe's free bytes less a reserve,
+    and within the cap `budget_bytes` of bytes in flight; a request larger than
+    the cap can never run and is rejected."""
 
-    def __init__(self, budget_bytes: int, max_batch_requests: int = 64, max_batch_segments: int = 1 << 24):
+    def __init__(self, budget_bytes: int, max_batch_requests: int = 64, max_batch_segments: int = 1 << 24,
+                 mem_probe=None, reserve_bytes: int = 1 << 30):
         self.budget_bytes = int(budget_bytes)
         self.max_batch_requests = int(max_batch_requests)
         self.max_batch_segments = int(max_batch_segments)
+        self.mem_probe = mem_probe
+        self.reserve_bytes = int(reserve_bytes)
+
+    def limit(self, bytes_in_use: int) -> int:
+        """Bytes in flight allowed now: the cap, and what the device has free."""
+        if self.mem_probe is None:
+            return self.budget_bytes
+        free = int(self.mem_probe())
+        return min(self.budget_bytes, bytes_in_use + max(0, free - self.reserve_bytes))
 
     def take(self, queue: collections.deque, bytes_in_use: int):
         batch, rejected = [], []
         used = bytes_in_use
         segs = 0
+        limit = self.limit(bytes_in_use)
         while queue and len(batch) < self.max_batch_requests:
             r = queue[0]
             if r.device_bytes > self.budget_bytes:
                 rejected.append(queue.popleft())
                 continue
-            if used + r.device_bytes > self.budget_bytes or (batch and segs + r.n > self.max_batch_segments):
+            if used + r.device_bytes > limit or (batch and segs + r.n > self.max_batch_segments):
                 break  # head of line waits for memory (keeps arrival order)
             batch.append(queue.popleft())
             used += r.device_bytes
@@ -128,9 +148,10 @@ class Server:
     (and may attach results to the requests)."""
 
     def __init__(self, launcher, budget_bytes: int, max_inflight: int = 4, max_batch_requests: int = 64,
-                 max_batch_segments: int = 1 << 24, clock=time.perf_counter, idle_sleep_s: float = 20e-6):
+                 max_batch_segments: int = 1 << 24, clock=time.perf_counter, idle_sleep_s: float = 20e-6,
+                 mem_probe=None, reserve_bytes: int = 1 << 30):
         self.launcher = launcher
-        self.admission = Admission(budget_bytes, max_batch_requests, max_batch_segments)
+        self.admission = Admission(budget_bytes, max_batch_requests, max_batch_segments, mem_probe, reserve_bytes)
         self.max_inflight = int(max_inflight)
         self.clock = clock
         self.idle_sleep_s = idle_sleep_s
@@ -213,6 +234,10 @@ class _Handle:
 
     def finish(self) -> int:
         status = int(self.keep["status"].item())
+        if status == 0:
+            base = self.keep["base"].cpu().numpy()  # per-scene voxel bases from the device scan
+            for k, r in enumerate(self.reqs):
+                r.voxels = int(base[k + 1] - base[k])
         if self.keep_results and status == 0:
             for r, m in zip(self.reqs, self.keep["masks"]):
                 r.result = m
@@ -260,15 +285,16 @@ class GpuLauncher:
                                                                    sum(r.piece_capacity for r in reqs)),
                              dtype=torch.uint8, device=self.device)
             status = torch.zeros(1, dtype=torch.int32, device=self.device)
+            base = torch.empty(len(reqs) + 1, dtype=torch.int64, device=self.device)
             st = vox.load().vox_generate_batched_ex(
                 vox._ptr(segs), n_total, vox._ptr(scenes), len(reqs), total_bricks, None, 0,
-                vox.OUT_BITMASK | vox.OUT_FRESH, None, vox._ptr(ws), ws.numel(), vox._ptr(status),
+                vox.OUT_BITMASK | vox.OUT_FRESH, vox._ptr(base), vox._ptr(ws), ws.numel(), vox._ptr(status),
                 vox._stream(stream))
             if st != vox.OK:
                 raise vox.VoxError(st, "vox_generate_batched_ex")
             ev = torch.cuda.Event()
             ev.record(stream)
-        keep = {"segs": segs, "masks": masks, "scenes": scenes, "ws": ws, "status": status}
+        keep = {"segs": segs, "masks": masks, "scenes": scenes, "ws": ws, "status": status, "base": base}
         return _Handle(ev, keep, reqs, self.keep_results)
 
 
@@ -285,10 +311,16 @@ def make_requests(stream_reqs, pool_size: int = 256, seed: int = 11):
         key = i % pool_size
         if key not in pool:
             w = rq.workload()
-            segs = torch.from_numpy(w.segs).pin_memory()
-            d = np.abs(w.segs[:, 3:].astype(np.int64) - w.segs[:, :3])
-            pool[key] = (segs, tuple(w.dims), int((d.max(axis=1) + 1).sum()) if w.n else 0)
-        segs, dims, voxels = pool[key]
-        out.append(ServeRequest(rid=i, arrival_s=rq.arrival_s, n=int(segs.shape[0]), dims=dims, segs_host=segs,
-                                voxels=voxels))
+            pool[key] = (torch.from_numpy(w.segs).pin_memory(), tuple(w.dims))
+        segs, dims = pool[key]
+        out.append(ServeRequest(rid=i, arrival_s=rq.arrival_s, n=int(segs.shape[0]), dims=dims, segs_host=segs))
     return out
+
+
+def gpu_free_bytes(device=None) -> int:
+    """Free device memory now: the driver's free bytes plus the bytes torch's
+    caching allocator holds but does not use (free for the next allocation)."""
+    import torch
+
+    free, _ = torch.cuda.mem_get_info(device)
+    return int(free + torch.cuda.memory_reserved(device) - torch.cuda.memory_allocated(device))

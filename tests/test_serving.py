@@ -99,3 +99,47 @@ def test_server_counts_device_failures():
     srv = Server(lambda b, s: Bad(1, [], b), budget_bytes=10**12, clock=FakeClock(), idle_sleep_s=0)
     st = srv.run(reqs)
     assert st.failed == 4 and st.completed == 0
+
+
+def test_admission_follows_the_memory_probe():
+    """With a memory probe, admission takes what the device has free (less the
+    reserve) under the cap, and waits when the probe says memory is short."""
+    import collections
+
+    reqs = make(6)
+    per = reqs[0].device_bytes
+    free = {"bytes": 2 * per + 100}
+    adm = Admission(budget_bytes=100 * per, max_batch_requests=10, mem_probe=lambda: free["bytes"],
+                    reserve_bytes=50)
+    q = collections.deque(reqs)
+    batch, rej = adm.take(q, bytes_in_use=0)
+    assert [r.rid for r in batch] == [0, 1] and not rej
+    free["bytes"] = 10  # the device filled up meanwhile
+    batch, _ = adm.take(q, bytes_in_use=2 * per)
+    assert batch == []
+    free["bytes"] = 3 * per + 50
+    batch, _ = adm.take(q, bytes_in_use=2 * per)
+    assert [r.rid for r in batch] == [2, 3, 4]
+
+
+def test_server_with_probe_completes_and_respects_free_memory():
+    reqs = make(30, gap=1e-4)
+    per = reqs[0].device_bytes
+    in_use = {"bytes": 0}
+    device_total = 4 * per
+
+    def launcher(batch, slot):
+        in_use["bytes"] += sum(r.device_bytes for r in batch)
+        assert in_use["bytes"] <= device_total, "admitted beyond the free memory"
+
+        class H(FakeHandle):
+            def finish(self):
+                in_use["bytes"] -= sum(r.device_bytes for r in self.reqs)
+                return 0
+
+        return H(3, [], batch)
+
+    srv = Server(launcher, budget_bytes=10**15, max_inflight=4, max_batch_requests=8, clock=FakeClock(),
+                 idle_sleep_s=0, mem_probe=lambda: device_total - in_use["bytes"], reserve_bytes=0)
+    st = srv.run(reqs)
+    assert st.completed == 30 and st.max_bytes_in_use <= device_total
