@@ -370,26 +370,51 @@ vox_status vox_generate_host(const vox_segment *h_segs, int64_t n, vox_dims dims
                              void *d_arena, size_t arena_bytes, int64_t *h_total, void *stream);
 
 /*
+ * vox_probe_red_or -- measurement helper; the paper has no counterpart. The
+ * per-voxel atomic volume issues one 32-bit OR reduction (red.or, result not
+ * returned, L2 asked to keep the line) per merged word; this call issues about
+ * `ops` of them at pseudo-random words of d_buf (words 32-bit words, at most
+ * 2^32; a per-thread linear congruential sequence from `seed` picks word and
+ * bit), on SMs x 8 CTAs of 256 threads, asynchronously on `stream`, so that a
+ * caller timing it with events gets the GPU's reduction throughput for a
+ * buffer of that size (L2-resident or not). The buffer's bits are OR-ed into;
+ * nothing else is written. vox_probe_red_or_ops(ops) is the exact number the
+ * call issues (ops rounded up to a multiple of the thread count).
+ * Errors: VOX_ERR_INVALID_ARG (null buffer, words out of range, ops < 0),
+ * VOX_ERR_ALIGNMENT, VOX_ERR_CUDA.
+ */
+vox_status vox_probe_red_or(uint32_t *d_buf, int64_t words, int64_t ops, uint32_t seed, void *stream);
+int64_t vox_probe_red_or_ops(int64_t ops);
+
+/*
  * vox_generate_noalloc -- vox_generate without a caller-provided workspace.
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory at the point where they voxelize, such as
- * code running while a stream is captured into a CUDA graph in global capture
- * mode (where cudaMalloc is not allowed), plug-ins inside a host application
- * that owns the whole device-memory budget through its own pool, or real-time
- * loops that cannot pay for cudaMalloc/cudaFree (cudaFree synchronises the
- * device). The caller still provides the segments, the outputs and the status
- * word, exactly as for vox_generate (same arguments, same results).
+ * plug-ins inside a host application that owns the whole device-memory budget
+ * through its own pool (a cudaMalloc behind its back can fail or break its
+ * accounting), or real-time loops that cannot pay for cudaMalloc/cudaFree
+ * (cudaFree synchronises the device). The caller still provides the segments,
+ * the outputs and the status word, as for vox_generate.
  *
- * Scratch: the count/scan scratch lives in a static device array inside the
- * library, VOX_NOALLOC_SCRATCH_BYTES bytes (about 15.3 MiB), which every GPU
- * that loads the library holds until the process exits. It is sized for at
- * most VOX_NOALLOC_MAX_SEGMENTS segments per call; a larger n returns
- * VOX_ERR_WORKSPACE at once and launches nothing. The call allocates nothing
- * (no cudaMalloc, cudaFree or allocating library routine).
+ * Path: the call runs exactly what vox_generate runs with a workspace of
+ * vox_workspace_size(n) bytes: count + scan, then the list and/or the volume
+ * by per-voxel atomics (never the brick path, whose arrays do not fit the
+ * scratch). So its outputs are those of that vox_generate call bit for bit,
+ * and VOX_OUT_BRICKED, which needs the brick path, returns VOX_ERR_WORKSPACE.
  *
- * Set-up: the first call on each device looks up the device address of the
- * array with cudaGetSymbolAddress, with that device current. Make that first
- * call outside any stream capture (for example once at start-up).
+ * Scratch: the count/scan scratch (scan tile counter and flags, offsets) lives
+ * in a static device array inside the library, VOX_NOALLOC_SCRATCH_BYTES bytes
+ * (about 15.3 MiB), which every GPU that loads the library holds until the
+ * process exits. It is sized for at most VOX_NOALLOC_MAX_SEGMENTS segments per
+ * call; a larger n returns VOX_ERR_WORKSPACE at once and launches nothing. The
+ * call allocates nothing (no cudaMalloc, cudaFree or allocating library
+ * routine).
+ *
+ * Set-up: the first call on each device (and again after the device's context
+ * is replaced, e.g. after cudaDeviceReset) looks up the device address of the
+ * array with cudaGetSymbolAddress, with that device current; the address is
+ * kept per device and context. Make that first call outside any stream
+ * capture (for example once at start-up).
  *
  * Sharing: every call on a device uses the same array, which keeps the
  * contents of the last call. Each call clears, with a stream-ordered memset,
@@ -412,20 +437,32 @@ vox_status vox_generate_noalloc(const vox_segment *d_segs, int64_t n, vox_dims d
  *                 16, 32 or 64 (0 = default: 32; 64-bit lists take 64 as 32);
  *                 longer runs pay the run's entry less often, shorter runs keep
  *                 more threads busy on small inputs
- *   volume_path   VOX_VOLUME_AUTO (bricks when the workspace allows) or
- *                 VOX_VOLUME_ATOMIC (always per-voxel atomics)
+ *   volume_path   VOX_VOLUME_AUTO (bricks when the workspace allows; pieces
+ *                 beyond the workspace by per-voxel atomics), VOX_VOLUME_ATOMIC
+ *                 (always per-voxel atomics: each thread merges the bits of
+ *                 consecutive voxels in one word into one reduction), or
+ *                 VOX_VOLUME_ATOMIC_WARP (always per-voxel atomics, the volume
+ *                 alone also merged across the warp: at every step the lanes
+ *                 holding equal words (__match_any_sync) OR their bits together
+ *                 (__reduce_or_sync) and one lane issues the reduction)
  *   ctas_per_sm   persistent CTAs per SM for the generation and brick kernels
  *                 (0 = the occupancy maximum; larger values are capped there)
- *   list_runs     32-bit list alone (no volume in the same launch): 0 = a
- *                 thread's run of run_len voxels continues into the next
- *                 segments (best when segments share one length that run_len
- *                 divides or that divides run_len), 1 = runs end at segment ends
- *                 (best for segments of varying length); other values are 0
+ *   list_runs     a list alone (no volume in the same launch, or the volume
+ *                 by bricks): 0 = a thread's run of run_len voxels continues
+ *                 into the next segments (best when segments share one length
+ *                 that run_len divides or that divides run_len); 1 = 32-bit
+ *                 lists only: runs end at segment ends (best for short segments
+ *                 of varying length); 2 = warp slices: each warp writes 1056
+ *                 consecutive voxels (lanes' runs of 33) in list order into
+ *                 shared memory and stores them with one TMA bulk copy, taking
+ *                 slices from a global work counter (32- and 64-bit lists; best
+ *                 for long segments); other values are 0
  * vox_set_tuning(NULL) restores the defaults. Not to be changed while calls
  * are being issued from other host threads.
  */
 #define VOX_VOLUME_AUTO 0
 #define VOX_VOLUME_ATOMIC 1
+#define VOX_VOLUME_ATOMIC_WARP 2
 typedef struct vox_tuning {
     int32_t run_len;
     int32_t volume_path;

@@ -8,9 +8,11 @@ later run with a similar workload reuses it without measuring.
 
 Tuned knobs (see include/vox.h, vox_tuning):
   run_len      voxels per thread run in the generation kernel (16, 32 or 64)
-  volume_path  bricks when the workspace allows (auto) or per-voxel atomics
+  volume_path  bricks when the workspace allows (auto), per-voxel atomics, or
+               per-voxel atomics merged across the warp
   ctas_per_sm  persistent CTAs per SM (0 = occupancy maximum, or fewer)
-  list_runs    32-bit list runs across segment ends (0) or cut at them (1)
+  list_runs    a list alone: thread runs across segment ends (0), 32-bit runs
+               cut at them (1), or warp slices stored by TMA bulk copies (2)
 """
 
 from __future__ import annotations
@@ -24,9 +26,10 @@ from . import vox
 CANDIDATES = [
     {"run_len": r, "volume_path": vp, "ctas_per_sm": c, "list_runs": 0}
     for r in (32, 64, 16)
-    for vp in (vox.VOLUME_AUTO, vox.VOLUME_ATOMIC)
+    for vp in (vox.VOLUME_AUTO, vox.VOLUME_ATOMIC, vox.VOLUME_ATOMIC_WARP)
     for c in (0, 2)
-] + [{"run_len": r, "volume_path": vox.VOLUME_AUTO, "ctas_per_sm": 0, "list_runs": 1} for r in (32, 64)]
+] + [{"run_len": r, "volume_path": vox.VOLUME_AUTO, "ctas_per_sm": 0, "list_runs": 1} for r in (32, 64)] + [
+    {"run_len": 32, "volume_path": vox.VOLUME_AUTO, "ctas_per_sm": c, "list_runs": 2} for c in (0, 4)]
 
 
 def default_cache_path() -> str:

@@ -18,6 +18,7 @@
 #include "vox_bricks.cuh"
 #include "vox_kernels.cuh"
 #include "vox_euclid.cuh"
+#include "vox_list.cuh"
 
 namespace {
 
@@ -27,6 +28,7 @@ constexpr size_t kWsAlign = 256;
 constexpr int64_t kMaxDim = int64_t(1) << 21;
 constexpr int64_t kMinPerCta = 2048;          // smallest voxel range given to one CTA
 constexpr int64_t kDefaultWaitNs = 500000000;  // 0.5 s bound on every in-kernel wait
+constexpr size_t kListCounterOffset = 128;    // k_list's chunk counter, in the workspace's ticket region
 
 std::atomic<int64_t> g_stall_tile{-1};
 std::atomic<int64_t> g_wait_ns{kDefaultWaitNs};
@@ -255,6 +257,40 @@ bool uses_bricks(int64_t n, vox_dims dims, size_t ws_bytes, BrickGeom *G, size_t
     return n > 0 && n < (int64_t(1) << 32) && make_geom(dims, G) && ws_bytes >= vol_layout(n, *G, 1, base).total;
 }
 
+int grid_ctas(const void *kernel, int threads, size_t smem);
+
+// The binning passes: persistent grids (SMs x CTAs per SM, no more CTAs than
+// 256-segment groups), threads striding over the segments.
+template <bool kEuclid, bool kBatched>
+vox_status launch_bin_t(const BinParams &bp, bool scatter, int64_t n, cudaStream_t stream)
+{
+    const void *k = scatter ? reinterpret_cast<const void *>(k_bin_scatter<kEuclid, kBatched>)
+                            : reinterpret_cast<const void *>(k_bin_count<kEuclid, kBatched>);
+    int grid = grid_ctas(k, 256, 0);
+    if (grid <= 0) return VOX_ERR_CUDA;
+    grid = static_cast<int>(std::min<int64_t>(grid, (n + 255) / 256));
+    if (scatter) k_bin_scatter<kEuclid, kBatched><<<static_cast<unsigned>(grid), 256, 0, stream>>>(bp);
+    else k_bin_count<kEuclid, kBatched><<<static_cast<unsigned>(grid), 256, 0, stream>>>(bp);
+    return cudaGetLastError() == cudaSuccess ? VOX_OK : VOX_ERR_CUDA;
+}
+
+vox_status launch_bin(const BinParams &bp, bool euclid, bool batched, bool scatter, int64_t n, cudaStream_t stream)
+{
+    if (batched) return launch_bin_t<false, true>(bp, scatter, n, stream);
+    if (euclid) return launch_bin_t<true, false>(bp, scatter, n, stream);
+    return launch_bin_t<false, false>(bp, scatter, n, stream);
+}
+
+vox_status launch_bin_count(const BinParams &bp, bool euclid, bool batched, int64_t n, cudaStream_t stream)
+{
+    return launch_bin(bp, euclid, batched, false, n, stream);
+}
+
+vox_status launch_bin_scatter(const BinParams &bp, bool euclid, bool batched, int64_t n, cudaStream_t stream)
+{
+    return launch_bin(bp, euclid, batched, true, n, stream);
+}
+
 // Count + scan. With a brick workspace it also zeroes the brick arrays and
 // counts every segment's pieces per brick (k_bin_count).
 vox_status launch_count_scan(const vox_segment *segs, int64_t n, vox_dims dims, int32_t *counts,
@@ -302,9 +338,7 @@ vox_status launch_count_scan(const vox_segment *segs, int64_t n, vox_dims dims, 
         bp.G = G;
         bp.brick_count = reinterpret_cast<int32_t *>(base + VL.count);
         bp.status = status;
-        const unsigned blocks = static_cast<unsigned>((n + 255) / 256);
-        if (euclid) k_bin_count<true><<<blocks, 256, 0, stream>>>(bp);
-        else k_bin_count<false><<<blocks, 256, 0, stream>>>(bp);
+        if (vox_status e = launch_bin_count(bp, euclid, false, n, stream)) return e;
     }
     return cudaGetLastError() == cudaSuccess ? VOX_OK : VOX_ERR_CUDA;
 }
@@ -352,11 +386,48 @@ vox_status launch_gen_t(const GenParams &p, cudaStream_t stream)
         if (tu.run_len == 16) return launch_gen_r<16, OUT, LIN64>(p, stream);
         if (tu.run_len == 64) return launch_gen_r<64, OUT, LIN64>(p, stream);
         return launch_gen_r<32, OUT, LIN64>(p, stream);
+    } else if constexpr (OUT == kOutMask) {
+        // the volume alone: per-lane word runs, or merged across the warp too
+        const vox_tuning tu = current_tuning();
+        if (tu.volume_path == VOX_VOLUME_ATOMIC_WARP) {
+            if (tu.run_len == 16) return launch_gen_r<16, OUT | kOutWarpDedup, LIN64>(p, stream);
+            if (tu.run_len == 64) return launch_gen_r<64, OUT | kOutWarpDedup, LIN64>(p, stream);
+            return launch_gen_r<32, OUT | kOutWarpDedup, LIN64>(p, stream);
+        }
+        if (tu.run_len == 16) return launch_gen_r<16, OUT, LIN64>(p, stream);
+        if (tu.run_len == 64) return launch_gen_r<64, OUT, LIN64>(p, stream);
+        return launch_gen_r<32, OUT, LIN64>(p, stream);
     } else {
         if (current_tuning().run_len == 16) return launch_gen_r<16, OUT, LIN64>(p, stream);
         if (current_tuning().run_len == 64) return launch_gen_r<64, OUT, LIN64>(p, stream);
         return launch_gen_r<32, OUT, LIN64>(p, stream);
     }
+}
+
+// The list alone by warp slices (k_list): persistent grid, the chunk counter in
+// the workspace's ticket region reset first.
+template <typename PackT>
+vox_status launch_list(const vox_segment *segs, int64_t n, void *list, int64_t capacity, void *ws, int32_t *status,
+                       cudaStream_t stream)
+{
+    const WsLayout L = ws_layout(n);
+    char *base = static_cast<char *>(ws);
+    ListParams p;
+    p.segs = reinterpret_cast<const int32_t *>(segs);
+    p.n = n;
+    p.offsets = reinterpret_cast<const int64_t *>(base + L.offsets);
+    p.list = list;
+    p.capacity = capacity;
+    p.status = status;
+    p.counter = reinterpret_cast<uint32_t *>(base + kListCounterOffset);
+    auto kernel = k_list<PackT>;
+    const size_t smem = sizeof(ListWarpSmem<PackT>) * kListWarps;
+    if (vox_status e = allow_smem(reinterpret_cast<const void *>(kernel), smem)) return e;
+    const int grid = grid_ctas(reinterpret_cast<const void *>(kernel), kListThreads, smem);
+    if (grid <= 0) return VOX_ERR_CUDA;
+    if (cudaMemsetAsync(p.counter, 0, sizeof(uint32_t), stream) != cudaSuccess) return VOX_ERR_CUDA;
+    kernel<<<static_cast<unsigned>(grid), kListThreads, smem, stream>>>(p);
+    return cudaGetLastError() == cudaSuccess ? VOX_OK : VOX_ERR_CUDA;
 }
 
 vox_status launch_generate(const vox_segment *segs, int64_t n, vox_dims dims, void *list, int64_t capacity,
@@ -389,6 +460,10 @@ vox_status launch_generate(const vox_segment *segs, int64_t n, vox_dims dims, vo
     // batched volumes may differ in size: 64-bit bit indices cover them all
     const bool lin64 = scene_of != nullptr || volume_bits(dims) > (uint64_t(1) << 32);
     const bool bm = flags & VOX_OUT_BITMASK;
+    if (!bm && current_tuning().list_runs == 2) {  // a list alone by warp slices
+        if (flags & VOX_OUT_LIST32) return launch_list<uint32_t>(segs, n, list, capacity, ws, status, stream);
+        if (flags & VOX_OUT_LIST64) return launch_list<uint64_t>(segs, n, list, capacity, ws, status, stream);
+    }
     if (flags & VOX_OUT_LIST32) {
         return bm ? launch_gen_t<kOutList32 | kOutMask, false>(p, stream) : launch_gen_t<kOutList32, false>(p, stream);
     }
@@ -426,7 +501,6 @@ vox_status launch_bricks(const vox_segment *segs, int64_t n, const BrickGeom &G,
     bp.status = status;
     const int sms = sm_count();
     if (sms <= 0) return VOX_ERR_CUDA;
-    const int64_t bin_blocks = (n + 255) / 256;
     ScanParams sp;
     sp.segs = nullptr;
     sp.counts_in = bp.brick_count;
@@ -447,8 +521,7 @@ vox_status launch_bricks(const vox_segment *segs, int64_t n, const BrickGeom &G,
     sp.n_scenes = 0;
     k_scan<false><<<static_cast<unsigned>(VL.n_tiles), kScanThreads, 0, stream>>>(sp);
     if (count_only) return cudaGetLastError() == cudaSuccess ? VOX_OK : VOX_ERR_CUDA;
-    if (euclid) k_bin_scatter<true><<<static_cast<unsigned>(bin_blocks), 256, 0, stream>>>(bp);
-    else k_bin_scatter<false><<<static_cast<unsigned>(bin_blocks), 256, 0, stream>>>(bp);
+    if (vox_status e = launch_bin_scatter(bp, euclid, false, n, stream)) return e;
     BrickParams brp;
     brp.segs = bp.segs;
     brp.G = G;
@@ -505,7 +578,7 @@ vox_status launch_outputs(const vox_segment *segs, int64_t n, vox_dims dims, voi
         return launch_bricks(segs, n, G, dims, mask, ws, ws_bytes, status, stream, false, true, true);
     }
     const bool bricks =
-        n > 0 && bm && current_tuning().volume_path != VOX_VOLUME_ATOMIC && uses_bricks(n, dims, ws_bytes, &G);
+        n > 0 && bm && current_tuning().volume_path == VOX_VOLUME_AUTO && uses_bricks(n, dims, ws_bytes, &G);
     if (!bricks) {
         // a fresh volume without the brick path: cleared first, then OR-ed into
         if (fresh && cudaMemsetAsync(mask, 0, 4 * static_cast<size_t>(vox_mask_words(dims)), stream) != cudaSuccess)
@@ -594,8 +667,7 @@ vox_status launch_batched_bricks(const vox_segment *segs, int64_t n_total, const
     bp.sb = sb;
     bp.scene_of = scene_of;
     bp.n_scenes = n_scenes;
-    const unsigned bin_blocks = static_cast<unsigned>((n_total + 255) / 256);
-    k_bin_count<false, true><<<bin_blocks, 256, 0, stream>>>(bp);
+    if (vox_status e = launch_bin_count(bp, false, true, n_total, stream)) return e;
     ScanParams sp{};
     sp.counts_in = bp.brick_count;
     sp.offsets_copy = bp.cursor;
@@ -610,7 +682,7 @@ vox_status launch_batched_bricks(const vox_segment *segs, int64_t n_total, const
     k_scan<false><<<static_cast<unsigned>(VL.n_tiles), kScanThreads, 0, stream>>>(sp);
     if (cudaGetLastError() != cudaSuccess) return VOX_ERR_CUDA;
     if (count_only) return VOX_OK;
-    k_bin_scatter<false, true><<<bin_blocks, 256, 0, stream>>>(bp);
+    if (vox_status e = launch_bin_scatter(bp, false, true, n_total, stream)) return e;
     BrickParams brp{};
     brp.segs = bp.segs;
     brp.G = BL.tot;
@@ -640,6 +712,23 @@ vox_status launch_batched_bricks(const vox_segment *segs, int64_t n_total, const
                            bp.brick_off + BL.tot.n_slots, capacity, scenes, scene_of, n_scenes);
 }
 
+// ---- measurement helper: red.or throughput ------------------------------------
+// Each thread issues `per_thread` 32-bit OR reductions (the instruction the
+// per-voxel atomic volume issues) at pseudo-random words of the buffer: a
+// per-thread linear congruential sequence x <- 1664525 x + 1013904223 (mod 2^32),
+// word = floor(x * words / 2^32), bit = x mod 32.
+__global__ void __launch_bounds__(256) k_probe_red_or(uint32_t *buf, uint64_t words, int64_t per_thread, uint32_t seed)
+{
+    uint64_t policy;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(policy));
+    uint32_t x = seed ^ ((blockIdx.x * blockDim.x + threadIdx.x) * 0x9E3779B9u);
+    for (int64_t i = 0; i < per_thread; ++i) {
+        x = x * 1664525u + 1013904223u;
+        const uint64_t idx = (static_cast<uint64_t>(x) * words) >> 32;
+        red_or_keep(buf + idx, 1u << (x & 31u), policy);
+    }
+}
+
 // ---- allocation-free variant: scratch in a static device array -------------
 // Same layout as ws_layout(VOX_NOALLOC_MAX_SEGMENTS): ticket region, tile
 // descriptors, offsets; each region rounded up to 256 bytes.
@@ -652,23 +741,57 @@ static_assert(kNoAllocScratchBytes == VOX_NOALLOC_SCRATCH_BYTES, "scratch size i
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
+// Unique id of the current device's current context (0 when none can be read):
+// a context that replaces an earlier one (after cudaDeviceReset) gets a new id
+// even if its handle value repeats.
+unsigned long long current_context_id()
+{
+    static std::mutex mu;
+    static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (get_current == nullptr || get_id == nullptr) {
+            void *f1 = nullptr, *f2 = nullptr;
+            cudaDriverEntryPointQueryResult q1, q2;
+            if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 4000, cudaEnableDefault, &q1) != cudaSuccess ||
+                q1 != cudaDriverEntryPointSuccess ||
+                cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+                q2 != cudaDriverEntryPointSuccess || f1 == nullptr || f2 == nullptr)
+                return 0;
+            get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(f1);
+            get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(f2);
+        }
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
 // Device address of the static scratch on the current device, looked up once
-// per device (host code must not use the symbol itself as a device pointer).
+// per device and context (host code must not use the symbol itself as a device
+// pointer; a context that replaces the device's earlier one reloads the module,
+// so its address is looked up again).
 vox_status noalloc_scratch(void **out)
 {
     static std::mutex mu;
-    static std::map<int, void *> cache;
+    static std::map<std::pair<int, unsigned long long>, void *> cache;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return VOX_ERR_CUDA;
+    // no context current yet (0): the lookup below creates it, and the next
+    // call finds it and caches
+    const unsigned long long ctx = current_context_id();
     std::lock_guard<std::mutex> lock(mu);
-    auto it = cache.find(dev);
+    const auto key = std::make_pair(dev, ctx);
+    auto it = ctx != 0 ? cache.find(key) : cache.end();
     if (it != cache.end()) {
         *out = it->second;
         return VOX_OK;
     }
     void *ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr) return VOX_ERR_CUDA;
-    cache[dev] = ptr;
+    if (ctx != 0) cache[key] = ptr;
     *out = ptr;
     return VOX_OK;
 }
@@ -832,11 +955,36 @@ vox_status vox_generate_noalloc(const vox_segment *d_segs, int64_t n, vox_dims d
                                 int64_t list_capacity, uint32_t *d_mask, int flags, int32_t *d_status, void *stream)
 {
     if (n > kNoAllocMaxSegments) return VOX_ERR_WORKSPACE;
-    if (n >= 0 && ws_layout(n).total > kNoAllocScratchBytes) return VOX_ERR_WORKSPACE;
+    if (n < 0) return VOX_ERR_INVALID_ARG;
+    if (ws_layout(n).total > kNoAllocScratchBytes) return VOX_ERR_WORKSPACE;
     void *scratch = nullptr;
     if (vox_status e = noalloc_scratch(&scratch)) return e;
-    return vox_generate(d_segs, n, dims, d_list, list_capacity, d_mask, flags, scratch, kNoAllocScratchBytes,
-                        d_status, stream);
+    // exactly the count/scan workspace of n segments: the same path as
+    // vox_generate with vox_workspace_size(n) bytes (per-voxel atomic volume)
+    return vox_generate(d_segs, n, dims, d_list, list_capacity, d_mask, flags, scratch, ws_layout(n).total, d_status,
+                        stream);
+}
+
+vox_status vox_probe_red_or(uint32_t *d_buf, int64_t words, int64_t ops, uint32_t seed, void *stream)
+{
+    if (d_buf == nullptr || words < 1 || words > (int64_t(1) << 32) || ops < 0) return VOX_ERR_INVALID_ARG;
+    if (!aligned(d_buf, 4)) return VOX_ERR_ALIGNMENT;
+    const int sms = sm_count();
+    if (sms <= 0) return VOX_ERR_CUDA;
+    const int64_t threads = static_cast<int64_t>(sms) * 8 * 256;
+    const int64_t per_thread = (ops + threads - 1) / threads;
+    if (per_thread == 0) return VOX_OK;
+    k_probe_red_or<<<static_cast<unsigned>(sms * 8), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        d_buf, static_cast<uint64_t>(words), per_thread, seed);
+    return cudaGetLastError() == cudaSuccess ? VOX_OK : VOX_ERR_CUDA;
+}
+
+int64_t vox_probe_red_or_ops(int64_t ops)
+{
+    const int sms = sm_count();
+    if (sms <= 0 || ops < 0) return 0;
+    const int64_t threads = static_cast<int64_t>(sms) * 8 * 256;
+    return (ops + threads - 1) / threads * threads;
 }
 
 size_t vox_workspace_size(int64_t n_segments)
@@ -891,8 +1039,7 @@ vox_status vox_count_bins(const vox_segment *d_segs, int64_t n, vox_dims dims, v
     bp.n = n;
     bp.G = G;
     bp.brick_count = reinterpret_cast<int32_t *>(base + VL.count);
-    k_bin_count<false><<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(bp);
-    return cudaGetLastError() == cudaSuccess ? VOX_OK : VOX_ERR_CUDA;
+    return launch_bin_count(bp, false, false, n, s);
 }
 
 vox_status vox_generate(const vox_segment *d_segs, int64_t n, vox_dims dims, void *d_list, int64_t list_capacity,
@@ -948,7 +1095,7 @@ vox_status vox_generate_batched_ex(const vox_segment *d_segs, int64_t n_total, c
     // the volumes by bricks when the caller gave the batch's brick count and the
     // workspace holds the brick arrays and a piece
     const bool bricks = bm && total_bricks > 0 && n_total > 0 && n_total < (int64_t(1) << 32) &&
-                        current_tuning().volume_path != VOX_VOLUME_ATOMIC &&
+                        current_tuning().volume_path == VOX_VOLUME_AUTO &&
                         ws_bytes >= batch_brick_layout(n_total, n_scenes, total_bricks, 1).VL.total;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     char *base = static_cast<char *>(d_ws);
@@ -1291,7 +1438,7 @@ vox_status vox_generate_host(const vox_segment *h_segs, int64_t n, vox_dims dims
     if (st != VOX_OK) return static_cast<vox_status>(st);
     if (has_list && V > list_capacity) return VOX_ERR_CAPACITY;
     BrickGeom G;
-    const bool bricks = bm && n > 0 && current_tuning().volume_path != VOX_VOLUME_ATOMIC &&
+    const bool bricks = bm && n > 0 && current_tuning().volume_path == VOX_VOLUME_AUTO &&
                         uses_bricks(n, dims, ws_bytes, &G);
     if (!bricks) {
         // one pass produces the list and the (cleared) volume together
@@ -1378,9 +1525,9 @@ void vox_set_tuning(const vox_tuning *t)
     }
     g_tuning = *t;
     if (g_tuning.run_len != 16 && g_tuning.run_len != 32 && g_tuning.run_len != 64) g_tuning.run_len = 0;
-    if (g_tuning.volume_path < 0 || g_tuning.volume_path > VOX_VOLUME_ATOMIC) g_tuning.volume_path = 0;
+    if (g_tuning.volume_path < 0 || g_tuning.volume_path > VOX_VOLUME_ATOMIC_WARP) g_tuning.volume_path = 0;
     if (g_tuning.ctas_per_sm < 0) g_tuning.ctas_per_sm = 0;
-    if (g_tuning.list_runs != 1) g_tuning.list_runs = 0;
+    if (g_tuning.list_runs != 1 && g_tuning.list_runs != 2) g_tuning.list_runs = 0;
 }
 
 void vox_get_tuning(vox_tuning *t)

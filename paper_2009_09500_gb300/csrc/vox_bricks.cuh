@@ -12,7 +12,7 @@
 // volume sector then crosses DRAM at most twice (read + write), whatever the
 // number of voxels in it.
 //
-//   k_bin_count    pieces per brick (one thread per segment, global atomics)
+//   k_bin_count    pieces per brick (lanes walk segments' pieces, global atomics)
 //   k_scan<false>  exclusive scan of the per-brick counts (decoupled look-back)
 //   k_bin_scatter  pieces written into their brick's bucket
 //   k_brick_volume one CTA per brick: voxels -> shared bitmap -> volume
@@ -191,35 +191,46 @@ struct AxisCrossings {
     }
 };
 
-// Calls f(brick, k_lo, len) for every maximal run of consecutive steps of the
-// segment that stays in one brick, in increasing k. Endpoints must be inside
-// the volume. Brick indices fit 32 bits (at most 2^26 bricks). kEuclid: the
-// steps are the samples of the Euclidean-N variant, N = int(|E - S|) (the
-// crossing formula holds for any N >= max |d_a|).
-template <bool kEuclid = false, typename F>
-__device__ __forceinline__ void for_each_piece(const int32_t *rec, const BrickGeom &G, F &&f)
-{
+// The maximal runs of consecutive steps of one segment that stay in one brick,
+// in increasing k: init() at the segment's start, then next() gives one run per
+// call. Endpoints must be inside the volume. Brick indices fit 32 bits (at most
+// 2^26 bricks). kEuclid: the steps are the samples of the Euclidean-N variant,
+// N = int(|E - S|) (the crossing formula holds for any N >= max |d_a|).
+template <bool kEuclid = false>
+struct PieceWalker {
     AxisCrossings ax[3];
-    int32_t A[3], bstep[3];
-    int32_t N = 0;
+    int32_t bstep[3];
+    int32_t brick, k, N;
+
+    __device__ __forceinline__ void init(const int32_t *rec, const BrickGeom &G)
+    {
+        int32_t A[3];
+        N = 0;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        A[a] = abs(rec[3 + a] - rec[a]);
-        N = max(N, A[a]);
-    }
-    if constexpr (kEuclid) N = euclid_steps(rec);
-    int32_t brick = (rec[0] >> G.logB[0]) + G.nb[0] * ((rec[1] >> G.logB[1]) + G.nb[1] * (rec[2] >> G.logB[2]));
-    const int32_t stride[3] = {1, G.nb[0], G.nb[0] * G.nb[1]};
+        for (int a = 0; a < 3; ++a) {
+            A[a] = abs(rec[3 + a] - rec[a]);
+            N = max(N, A[a]);
+        }
+        if constexpr (kEuclid) N = euclid_steps(rec);
+        brick = (rec[0] >> G.logB[0]) + G.nb[0] * ((rec[1] >> G.logB[1]) + G.nb[1] * (rec[2] >> G.logB[2]));
+        const int32_t stride[3] = {1, G.nb[0], G.nb[0] * G.nb[1]};
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        ax[a].init(rec[a], rec[3 + a], A[a], N, G.logB[a]);
-        bstep[a] = rec[3 + a] >= rec[a] ? stride[a] : -stride[a];
+        for (int a = 0; a < 3; ++a) {
+            ax[a].init(rec[a], rec[3 + a], A[a], N, G.logB[a]);
+            bstep[a] = rec[3 + a] >= rec[a] ? stride[a] : -stride[a];
+        }
+        k = 0;
     }
-    int32_t k = 0;
-    while (true) {
+
+    // The current run (brick b, first step k_lo, len steps); advances to the
+    // next one and returns false if this run was the segment's last.
+    __device__ __forceinline__ bool next(int32_t &b, int32_t &k_lo, int32_t &len)
+    {
         const int32_t kn = min(min(ax[0].nk, ax[1].nk), min(ax[2].nk, N + 1));
-        f(brick, k, kn - k);
-        if (kn > N) break;
+        b = brick;
+        k_lo = k;
+        len = kn - k;
+        if (kn > N) return false;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             if (ax[a].nk == kn) {
@@ -228,8 +239,29 @@ __device__ __forceinline__ void for_each_piece(const int32_t *rec, const BrickGe
             }
         }
         k = kn;
+        return true;
+    }
+};
+
+// Calls f(brick, k_lo, len) for every maximal run of consecutive steps of the
+// segment that stays in one brick, in increasing k (PieceWalker in a loop).
+template <bool kEuclid = false, typename F>
+__device__ __forceinline__ void for_each_piece(const int32_t *rec, const BrickGeom &G, F &&f)
+{
+    PieceWalker<kEuclid> pw;
+    pw.init(rec, G);
+    bool more = true;
+    while (more) {
+        int32_t b, k_lo, len;
+        more = pw.next(b, k_lo, len);
+        f(b, k_lo, len);
     }
 }
+
+// Pieces are at most kPieceMaxLen steps long: a longer run in one brick is cut
+// into parts of kPieceMaxLen (the last one shorter), so that no lane of the
+// brick kernel walks a long piece while the rest of its CTA waits.
+constexpr int32_t kPieceMaxLen = 64;
 
 // piece = segment (32 bits) | first step (22 bits) | length - 1 (10 bits)
 __device__ __forceinline__ uint64_t pack_piece(int64_t seg, int32_t k_lo, int32_t len)
@@ -284,7 +316,44 @@ __device__ __forceinline__ void load_record(const int32_t *segs, int64_t s, int3
     r[0] = a.x; r[1] = a.y; r[2] = b.x; r[3] = b.y; r[4] = c.x; r[5] = c.y;
 }
 
-// One segment per thread.
+// Binning work loop, shared by the counting and the scattering pass: a
+// persistent grid whose threads take segments s = t, t + T, t + 2T, ... (T the
+// grid's threads) and walk each one's pieces. A thread then sums the work of
+// about n / T segments, so that with lengths of any mix the threads of a warp
+// carry similar totals (one segment per thread would leave a warp waiting for
+// its longest segment). emit(slot, seg, k_lo, len) is called for every piece
+// (runs in one brick cut to at most kPieceMaxLen steps) with its slot in the
+// batch's slot numbering. A segment with an endpoint outside its volume has no
+// pieces (the count kernel reports it).
+template <bool kEuclid, bool kBatched, typename Emit>
+__device__ __forceinline__ void bin_loop(const BinParams &p, Emit &&emit)
+{
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; s < p.n; s += stride) {
+        int64_t slot_base;
+        const BrickGeom *Gp = segment_geom<kBatched>(p, s, slot_base);
+        if (Gp == nullptr) continue;
+        int32_t r[6];
+        load_record(p.segs, s, r);
+        if (!endpoints_inside(r, *Gp)) continue;
+        const int32_t rep = static_cast<int32_t>(s) & (Gp->reps - 1);
+        PieceWalker<kEuclid> pw;
+        pw.init(r, *Gp);
+        bool more = true;
+        while (more) {
+            int32_t b, k_lo, len;
+            more = pw.next(b, k_lo, len);
+            while (len > 0) {
+                const int32_t part = min(len, kPieceMaxLen);
+                emit(slot_base + piece_slot(*Gp, b, part, rep), s, k_lo, part);
+                k_lo += part;
+                len -= part;
+            }
+        }
+    }
+}
+
+// Pieces per slot (persistent grid).
 template <bool kEuclid, bool kBatched = false>
 __global__ void __launch_bounds__(256) k_bin_count(BinParams p)
 {
@@ -292,43 +361,24 @@ __global__ void __launch_bounds__(256) k_bin_count(BinParams p)
     // that resets the status word); it reads only the segments and the host's
     // geometry, writes only the slot counts, and skips segments with endpoints
     // outside the volume (reported by the count kernel)
-    const int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (s >= p.n) return;
     // a batch reads the scene map and numbering, valid only without an error
     if (kBatched && ld_volatile_i32(p.status) != 0) return;
-    int64_t slot_base;
-    const BrickGeom *Gp = segment_geom<kBatched>(p, s, slot_base);
-    if (Gp == nullptr) return;
-    const BrickGeom G = *Gp;  // in registers: the atomics below cannot alias it
-    int32_t r[6];
-    load_record(p.segs, s, r);
-    if (!endpoints_inside(r, G)) return;
-    const int32_t rep = static_cast<int32_t>(s) & (G.reps - 1);
-    for_each_piece<kEuclid>(r, G, [&](int32_t b, int32_t, int32_t len) {
-        atomicAdd(p.brick_count + slot_base + piece_slot(G, b, len, rep), 1);
+    bin_loop<kEuclid, kBatched>(p, [&](int64_t slot, int64_t, int32_t, int32_t) {
+        atomicAdd(p.brick_count + slot, 1);
     });
 }
 
-// One segment per thread. p.G.n_slots: the number of slots (all scenes' when batched).
+// Pieces written into their slots (persistent grid). p.G.n_slots: the number of
+// slots (all scenes' when batched). Slot reservations of up to four pieces are
+// in flight together before their stores, so the returning atomics' latency
+// overlaps.
 template <bool kEuclid, bool kBatched = false>
 __global__ void __launch_bounds__(256) k_bin_scatter(BinParams p)
 {
-    using SlotT = typename std::conditional<kBatched, int64_t, uint32_t>::type;
-    const int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (s >= p.n || ld_volatile_i32(p.status) != 0) return;
+    if (ld_volatile_i32(p.status) != 0) return;
     if (__ldg(p.brick_off + p.G.n_slots) > p.capacity) return;  // the volume falls back to atomics
-    int64_t slot_base;
-    const BrickGeom *Gp = segment_geom<kBatched>(p, s, slot_base);
-    if (Gp == nullptr) return;
-    const BrickGeom G = *Gp;  // in registers: the atomics and stores below cannot alias it
-    const int32_t rep = static_cast<int32_t>(s) & (G.reps - 1);
-    int32_t r[6];
-    load_record(p.segs, s, r);
-    if (!endpoints_inside(r, G)) return;
-    // slot reservations of up to four pieces are in flight together before
-    // their stores, so the returning atomics' latency overlaps
     constexpr int kBatch = 4;
-    SlotT bb[kBatch];
+    int64_t bb[kBatch];
     uint64_t val[kBatch];
     int nb = 0;
     auto flush = [&]() {
@@ -341,12 +391,12 @@ __global__ void __launch_bounds__(256) k_bin_scatter(BinParams p)
             if (e < nb) p.pieces[pos[e]] = val[e];
         nb = 0;
     };
-    for_each_piece<kEuclid>(r, G, [&](int32_t b, int32_t k, int32_t len) {
+    bin_loop<kEuclid, kBatched>(p, [&](int64_t slot, int64_t seg, int32_t k, int32_t len) {
 #pragma unroll
         for (int e = 0; e < kBatch; ++e)
             if (e == nb) {
-                bb[e] = static_cast<SlotT>(slot_base + piece_slot(G, b, len, rep));
-                val[e] = pack_piece(s, k, len);
+                bb[e] = slot;
+                val[e] = pack_piece(seg, k, len);
             }
         if (++nb == kBatch) flush();
     });

@@ -183,6 +183,35 @@ __device__ __forceinline__ uint32_t add_carry(uint32_t &x, uint32_t y)
     return c;
 }
 
+// P += dm + cb db + cc dc (mod 2^bits) for carries cb, cc in {0, 1}: the packed
+// word moves one voxel along the major axis and along each minor axis whose
+// carry is set. 32-bit words: three integer adds; 64-bit words: one add and two
+// multiply-adds by the carry, each chained through the carry flag from the low
+// to the high half.
+__device__ __forceinline__ void advance_packed(uint32_t &P, uint32_t dm, uint32_t cb, uint32_t db, uint32_t cc,
+                                               uint32_t dc)
+{
+    P += dm + cb * db + cc * dc;
+}
+
+__device__ __forceinline__ void advance_packed(uint64_t &P, uint64_t dm, uint32_t cb, uint64_t db, uint32_t cc,
+                                               uint64_t dc)
+{
+    asm("{\n\t.reg .u32 lo, hi;\n\t"
+        "mov.b64 {lo, hi}, %0;\n\t"
+        "add.cc.u32 lo, lo, %1;\n\t"
+        "addc.u32 hi, hi, %2;\n\t"
+        "mad.lo.cc.u32 lo, %3, %4, lo;\n\t"
+        "madc.lo.u32 hi, %3, %5, hi;\n\t"
+        "mad.lo.cc.u32 lo, %6, %7, lo;\n\t"
+        "madc.lo.u32 hi, %6, %8, hi;\n\t"
+        "mov.b64 %0, {lo, hi};\n\t}"
+        : "+l"(P)
+        : "r"(static_cast<uint32_t>(dm)), "r"(static_cast<uint32_t>(dm >> 32)), "r"(cb),
+          "r"(static_cast<uint32_t>(db)), "r"(static_cast<uint32_t>(db >> 32)), "r"(cc),
+          "r"(static_cast<uint32_t>(dc)), "r"(static_cast<uint32_t>(dc >> 32)));
+}
+
 // Stepping state of one segment. PackT: uint32_t (LIST32) or uint64_t (LIST64);
 // LinT: uint32_t or uint64_t volume bit index (volumes up to or beyond 2^32 bits).
 // The three minor/major roles are fixed at entry: the major axis (|d| = N) moves
@@ -254,13 +283,12 @@ struct Stepper {
     template <bool kP, bool kL>
     __device__ __forceinline__ void step()
     {
-        if (kP) P += dPm;
         if (kL) L += dLm;
         const uint32_t cb = add_carry(eb, Ab2);
         const uint32_t cc = add_carry(ec, Ac2);
         eb += cb * bias;
         ec += cc * bias;
-        if (kP) P += static_cast<PackT>(cb) * dPb + static_cast<PackT>(cc) * dPc;
+        if (kP) advance_packed(P, dPm, cb, dPb, cc, dPc);
         if (kL) L += static_cast<LinT>(cb) * dLb + static_cast<LinT>(cc) * dLc;
     }
 };

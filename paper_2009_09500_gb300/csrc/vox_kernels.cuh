@@ -248,7 +248,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(ScanParams p)
 
 // ------------------------------------------------------------------ generation
 // kOutSegRuns: with kOutList32 alone, runs cut at segment ends (launch tuning list_runs)
-enum : int { kOutList32 = 1, kOutList64 = 2, kOutMask = 4, kOutSegRuns = 8 };
+// kOutWarpDedup: with kOutMask alone, words merged across the warp before their atomics
+enum : int { kOutList32 = 1, kOutList64 = 2, kOutMask = 4, kOutSegRuns = 8, kOutWarpDedup = 16 };
 
 struct GenParams {
     const int32_t *segs;     // [n][6], 16-byte aligned
@@ -403,6 +404,20 @@ __device__ __forceinline__ void red_or_keep(uint32_t *addr, uint32_t bits, uint6
                  : "memory");
 }
 
+// Warp-aggregated OR: the lanes with `pred` each hold (addr, bits); lanes with the
+// same word address form a group (__match_any_sync), the group's bits are OR-ed
+// together (__reduce_or_sync), and the group's first lane issues one reduction
+// for the group. Called by the whole warp (converged).
+__device__ __forceinline__ void warp_red_or(bool pred, uint32_t *addr, uint32_t bits, uint64_t policy)
+{
+    const uint32_t fm = __ballot_sync(0xffffffffu, pred);
+    if (pred) {
+        const uint32_t grp = __match_any_sync(fm, reinterpret_cast<unsigned long long>(addr));
+        const uint32_t all = __reduce_or_sync(grp, bits);
+        if ((threadIdx.x & 31) == static_cast<unsigned>(__ffs(grp) - 1)) red_or_keep(addr, all, policy);
+    }
+}
+
 template <int R, int OUT, bool LIN64>
 __global__ void __launch_bounds__(kGenThreads, 3) k_generate(GenParams p)
 {
@@ -411,6 +426,8 @@ __global__ void __launch_bounds__(kGenThreads, 3) k_generate(GenParams p)
     using LinT = typename std::conditional<LIN64, uint64_t, uint32_t>::type;
     constexpr bool kList = L::kList;
     constexpr bool kMask = (OUT & kOutMask) != 0;
+    constexpr bool kWarpDedup = (OUT & kOutWarpDedup) != 0;
+    static_assert(!kWarpDedup || OUT == (kOutMask | kOutWarpDedup), "warp-merged atomics: volume alone");
     constexpr int kPass = kGenThreads * R;
     constexpr int S = L::S;
     static_assert(R % 4 == 0 && 32 % R == 0 || R == 32 || R == 64, "run length");
@@ -573,6 +590,52 @@ __global__ void __launch_bounds__(kGenThreads, 3) k_generate(GenParams p)
                     }
                     __syncthreads();
                 }
+            }
+        } else if constexpr (kWarpDedup) {
+            // the volume alone, words merged across the warp: thread t takes the R
+            // consecutive voxels from gp + t R as below, but the warp walks its 32
+            // runs in step (R iterations, finished lanes idle), so that at every
+            // step the lanes whose word just ended can merge it with the other
+            // lanes' equal words before one reduction per distinct word
+            for (int64_t gp = g0; gp < g_end; gp += kPass) {
+                const int64_t g = gp + static_cast<int64_t>(t) * R;
+                const int32_t len = g < g_end ? static_cast<int32_t>(min64(R, g_end - g)) : 0;
+                Stepper<PackT, LinT> st;
+                int32_t j = 0, left = 0;
+                if (len > 0) {
+                    j = find_in_window(sm.offs, cnt, g);
+                    if (batched) VOX_USE_SCENE_OF(s_base + j);
+                    const int32_t k = static_cast<int32_t>(g - sm.offs[j]);
+                    st.enter(sm.recs + 6 * j, k, w, wh);
+                    left = st.left;
+                }
+                uint32_t *cur = nullptr;  // the word being filled (address) and its bits
+                uint32_t acc = 0;
+                for (int32_t u = 0; u < R; ++u) {
+                    uint32_t *fw = nullptr;
+                    uint32_t fb = 0;
+                    if (u < len) {
+                        uint32_t *const word = mask_s + (st.L >> 5);
+                        if (word != cur) {
+                            fw = cur;
+                            fb = acc;
+                            cur = word;
+                            acc = 0;
+                        }
+                        acc |= 1u << (static_cast<uint32_t>(st.L) & 31u);
+                        if (left > 0) {
+                            st.template step<false, true>();
+                            --left;
+                        } else if (u + 1 < len) {  // the run continues in the next segment
+                            ++j;
+                            if (batched) VOX_USE_SCENE_OF(s_base + j);
+                            st.enter(sm.recs + 6 * j, 0, w, wh);
+                            left = st.left;
+                        }
+                    }
+                    warp_red_or(fb != 0 && mask_s != nullptr && fw != nullptr, fw, fb, keep_policy);
+                }
+                warp_red_or(acc != 0 && mask_s != nullptr && cur != nullptr, cur, acc, keep_policy);
             }
         } else
         // ---- passes over [g0, g_end): thread t takes the R consecutive voxels

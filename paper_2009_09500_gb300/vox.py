@@ -44,11 +44,12 @@ EXPORTED = (
     "vox_mask_words_bricked", "vox_brick_shape", "vox_unbrick",
     "vox_euclid_workspace_size", "vox_euclid_generate", "vox_euclid_plan", "vox_euclid_workspace_size_volume",
     "vox_count_bins", "vox_scene_bricks", "vox_workspace_size_batched_volume", "vox_generate_batched_ex",
-    "vox_plan_batched",
+    "vox_plan_batched", "vox_probe_red_or", "vox_probe_red_or_ops",
 )
 
 VOLUME_AUTO = 0
 VOLUME_ATOMIC = 1
+VOLUME_ATOMIC_WARP = 2
 
 
 class Tuning(ctypes.Structure):
@@ -148,6 +149,10 @@ def load(path: str | None = None):
     lib.vox_get_tuning.restype = None
     lib.vox_generate_noalloc.argtypes = [vp, i64, Dims, vp, i64, vp, i32, vp, vp]
     lib.vox_generate_noalloc.restype = i32
+    lib.vox_probe_red_or.argtypes = [vp, i64, i64, ctypes.c_uint32, vp]
+    lib.vox_probe_red_or.restype = i32
+    lib.vox_probe_red_or_ops.argtypes = [i64]
+    lib.vox_probe_red_or_ops.restype = i64
     if path == _build.LIB:
         _lib = lib
     return lib
@@ -314,11 +319,20 @@ def vox_generate_from_scan(segs, dims, ws, status, list_out=None, mask=None, fla
 
 def vox_generate_noalloc(segs, dims, status, list_out=None, mask=None, flags=None, stream=None, capacity=None):
     """vox_generate for callers that cannot allocate device memory: the scratch
-    is the library's static device array (at most NOALLOC_MAX_SEGMENTS segments
-    per call). Calls that overlap on the GPU share that array and race."""
+    is the library's static device array, so a call takes at most
+    NOALLOC_MAX_SEGMENTS segments (more raise VoxError with VOX_ERR_WORKSPACE,
+    naming the limit, before anything is launched). The path is vox_generate's
+    with a workspace of vox_workspace_size(n) bytes (volume by per-voxel
+    atomics; VOX_OUT_BRICKED is refused with VOX_ERR_WORKSPACE). Calls that
+    overlap on the GPU share that array and race."""
     import torch
 
     _check_segs(segs)
+    if segs.shape[0] > NOALLOC_MAX_SEGMENTS:
+        err = VoxError(ERR_WORKSPACE, "vox_generate_noalloc")
+        err.args = (f"vox_generate_noalloc: {segs.shape[0]} segments exceed the static scratch's limit of "
+                    f"{NOALLOC_MAX_SEGMENTS} segments per call (status {ERR_WORKSPACE})",)
+        raise err
     if flags is None:
         flags = 0
         if list_out is not None:
@@ -329,6 +343,15 @@ def vox_generate_noalloc(segs, dims, status, list_out=None, mask=None, flags=Non
     st = load().vox_generate_noalloc(_ptr(segs), segs.shape[0], _dims(dims), _ptr(list_out), cap, _ptr(mask),
                                      int(flags), _ptr(status), _stream(stream))
     _check(st, "vox_generate_noalloc")
+
+
+def vox_probe_red_or(buf, ops: int, seed: int = 1, stream=None) -> int:
+    """Issue about `ops` red.or reductions at pseudo-random words of the device
+    int32 tensor `buf` (measurement helper, asynchronous); returns the exact count."""
+    lib = load()
+    st = lib.vox_probe_red_or(_ptr(buf), buf.numel(), int(ops), int(seed) & 0xffffffff, _stream(stream))
+    _check(st, "vox_probe_red_or")
+    return int(lib.vox_probe_red_or_ops(int(ops)))
 
 
 def vox_host_arena_size(n: int, dims, flags: int, capacity: int) -> int:

@@ -31,6 +31,8 @@ def test_tuning_set_get_and_sanitised():
     try:
         vox.vox_set_tuning(16, vox.VOLUME_ATOMIC, 2, 1)
         assert vox.vox_get_tuning() == {"run_len": 16, "volume_path": 1, "ctas_per_sm": 2, "list_runs": 1}
+        vox.vox_set_tuning(32, vox.VOLUME_ATOMIC_WARP, 0, 2)
+        assert vox.vox_get_tuning() == {"run_len": 32, "volume_path": 2, "ctas_per_sm": 0, "list_runs": 2}
         vox.vox_set_tuning(7, 9, -3, 5)
         assert vox.vox_get_tuning() == {"run_len": 0, "volume_path": 0, "ctas_per_sm": 0, "list_runs": 0}
     finally:
@@ -40,5 +42,5 @@ def test_tuning_set_get_and_sanitised():
 
 def test_candidates_cover_the_knobs():
     keys = {(c["run_len"], c["volume_path"], c["ctas_per_sm"], c["list_runs"]) for c in autotune.CANDIDATES}
-    assert {16, 32, 64} == {k[0] for k in keys} and {0, 1} == {k[1] for k in keys} and len(keys) == 14
-    assert {0, 1} == {k[3] for k in keys}
+    assert {16, 32, 64} == {k[0] for k in keys} and {0, 1, 2} == {k[1] for k in keys} and len(keys) == 22
+    assert {0, 1, 2} == {k[3] for k in keys}

@@ -82,3 +82,55 @@ def test_segment_cut_runs_bit_exact(run_len):
             assert (got[len(want):] == np.uint32(0xffffffff)).all(), "written past the list"
     finally:
         vox.vox_reset_tuning()
+
+
+@pytest.mark.parametrize("wide", [False, True])
+def test_warp_slice_list_bit_exact(wide):
+    """Lists alone by warp slices (list_runs = 2), 32- and 64-bit: lengths up to
+    the volume edge, runs of one-voxel segments (slices spanning many windows of
+    32 segments), long segments spanning many slices, a ragged list end; the
+    whole list against the oracle, nothing written past it; a capacity error
+    writes nothing."""
+    from paper_2009_09500_gb300 import build
+
+    build.build_library()
+    rng = np.random.default_rng(14 + wide)
+    edge = 4096 if wide else 1024
+    parts = [
+        workloads._segments_from_major(rng, rng.integers(0, edge, 6000), edge),
+        workloads._segments_from_major(rng, np.zeros(5000, np.int64), edge),
+        workloads._segments_from_major(rng, rng.integers(0, 40, 20000), edge),
+        workloads._segments_from_major(rng, np.full(30, edge - 1, np.int64), edge),
+    ]
+    segs_np = np.concatenate(parts)
+    segs_np = segs_np[rng.permutation(segs_np.shape[0])]
+    dims = (edge, edge, edge)
+    O = get_oracle()
+    if O.total(segs_np) % 4 == 0:  # a ragged end: the last slice's tail by plain stores
+        segs_np = np.concatenate([segs_np, segs_np[:1] * 0])
+    want = O.list64(segs_np) if wide else O.list32(segs_np)
+    V = len(want)
+    assert V % 4 != 0
+    segs = torch.from_numpy(np.ascontiguousarray(segs_np)).cuda()
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ws = torch.empty(vox.vox_workspace_size(segs.shape[0]), dtype=torch.uint8, device="cuda")
+    dt = torch.int64 if wide else torch.int32
+    lst = torch.full((V + 64,), -1, dtype=dt, device="cuda")
+    flag = vox.OUT_LIST64 if wide else vox.OUT_LIST32
+    try:
+        vox.vox_set_tuning(32, 0, 0, 2)
+        for _ in range(2):  # twice: the chunk counter is reset per launch
+            lst.fill_(-1)
+            vox.vox_generate(segs, dims, ws, st, lst, None, flag, capacity=V)
+            torch.cuda.synchronize()
+            assert int(st.item()) == 0
+            got = lst.cpu().numpy().view(want.dtype)
+            assert np.array_equal(got[:V], want)
+            assert (got[V:] == np.array(-1, dtype=np.int64).astype(want.dtype)).all(), "written past the list"
+        lst.fill_(-1)
+        vox.vox_generate(segs, dims, ws, st, lst, None, flag, capacity=V - 1)
+        torch.cuda.synchronize()
+        assert int(st.item()) == vox.ERR_CAPACITY
+        assert (lst.cpu().numpy() == -1).all(), "nothing may be written on a capacity error"
+    finally:
+        vox.vox_reset_tuning()
