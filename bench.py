@@ -850,7 +850,7 @@ def measure_euclid(w, dev, stream, flush, reps: int) -> dict:
                     "walk) + fresh volume (bricks); L2 flushed between calls"}
 
 
-def measure_atomics(dev, stream, flush, reps: int) -> dict:
+def measure_atomics(dev, stream, flush, reps: int, big: bool = True) -> dict:
     """The per-voxel atomic volume against the GPU's red.or throughput. The
     microbenchmark (vox_probe_red_or: 32-bit OR reductions at pseudo-random
     words) on a 128 MiB buffer (the fixed-length batch's 1024^3 volume, about
@@ -878,7 +878,7 @@ def measure_atomics(dev, stream, flush, reps: int) -> dict:
         return float(np.median(ts))
 
     micro = {}
-    for name, words in (("128MiB", 32 << 20), ("8GiB", 2 << 30)):
+    for name, words in (("128MiB", 32 << 20), ("8GiB", 2 << 30))[:2 if big else 1]:
         buf = torch.zeros(words, dtype=torch.int32, device=dev)
         ops = vox.vox_probe_red_or_ops(1 << 28)
         ms = timed(lambda: vox.vox_probe_red_or(buf, 1 << 28, 7, stream))
@@ -951,7 +951,8 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     if args.only == "atomics":  # one section alone (e.g. under a profiler)
-        print(json.dumps({"atomic_volume": measure_atomics(dev, stream, flush, min(args.steps, 10))}), flush=True)
+        print(json.dumps({"atomic_volume": measure_atomics(dev, stream, flush, min(args.steps, 10),
+                                                           big=not args.no_big_probe)}), flush=True)
         return 0
 
     # headline: each rank voxelizes its own arbitrary-length batch (weak scaling)
@@ -1054,6 +1055,7 @@ def main():
     ap.add_argument("--no-latency", action="store_true")
     ap.add_argument("--no-atomics", action="store_true")
     ap.add_argument("--only", choices=["atomics"], default=None, help="run one section alone and print it")
+    ap.add_argument("--no-big-probe", action="store_true", help="atomics: skip the 8 GiB red.or probe")
     ap.add_argument("--tuning", default="", help="run_len,volume_path,ctas_per_sm[,list_runs]: use this launch tuning")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
