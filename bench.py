@@ -931,6 +931,16 @@ def measure_atomics(dev, stream, flush, reps: int, big: bool = True) -> dict:
                     "L2 flushed between calls"}
 
 
+def _section(name, fn, *a, **kw):
+    """An auxiliary measurement: its result, or the error it raised (so that one
+    failing side measurement does not lose the headline line)."""
+    try:
+        return fn(*a, **kw)
+    except Exception as e:  # noqa: BLE001 - reported in the JSON line
+        print(f"section {name} failed: {e!r}", file=sys.stderr, flush=True)
+        return {"error": f"{type(e).__name__}: {e}"}
+
+
 def run_ours(args):
     import torch
 
@@ -968,7 +978,7 @@ def run_ours(args):
     main_tuning = vox.vox_get_tuning()
     bricked = None
     if not args.no_bricked and world == 1:
-        bricked = measure_bricked(sb, stream, flush, min(args.steps, 10))
+        bricked = _section("bricked", measure_bricked, sb, stream, flush, min(args.steps, 10))
         bricked["row_major_volume_ms"] = s3["kernels_ms"]["volume"]
     V3, P3 = sb.V, sb.P
     sb.free()
@@ -976,7 +986,7 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         e2e = measure_e2e(w3, vox.OUT_LIST64, P3, 3, dev, stream)
-        e2e["value"] = e2e["value"] * world  # every rank moves its own batch
+        e2e["value"] = e2e["value"] * world  # every rank moves its own batch (the headline e2e: not guarded)
     # the fixed-length batch, with its own tuning and roofline
     cfg2 = None
     if not args.no_config2:
@@ -989,21 +999,22 @@ def run_ours(args):
         sb2.free()
         del sb2
         if not args.no_euclid and world == 1:
-            cfg2["euclid_variant"] = measure_euclid(w2, dev, stream, flush, min(args.steps, 20))
-    latency = measure_latency(dev, stream) if world == 1 and not args.no_latency else None
-    atomics = measure_atomics(dev, stream, flush, min(args.steps, 10)) if world == 1 and not args.no_atomics else None
+            cfg2["euclid_variant"] = _section("euclid", measure_euclid, w2, dev, stream, flush, min(args.steps, 20))
+    latency = _section("latency", measure_latency, dev, stream) if world == 1 and not args.no_latency else None
+    atomics = (_section("atomics", measure_atomics, dev, stream, flush, min(args.steps, 10))
+               if world == 1 and not args.no_atomics else None)
     batched = None
     if not args.no_batched and world == 1:
-        batched = measure_batched(args.steps, dev, tune=not args.tuning)  # serving keeps the batch's tuning
+        batched = _section("batched", measure_batched, args.steps, dev, tune=not args.tuning)  # serving keeps its tuning
     served = None
     if not args.no_serve and world == 1:
-        served = [measure_serving(args.serve_seconds, 2000.0, dev),
-                  measure_serving(args.serve_seconds / 2, 6000.0, dev)]
+        served = [_section("serving", measure_serving, args.serve_seconds, 2000.0, dev),
+                  _section("serving", measure_serving, args.serve_seconds / 2, 6000.0, dev)]
     vox.vox_set_tuning(main_tuning["run_len"], main_tuning["volume_path"], main_tuning["ctas_per_sm"],
                        main_tuning["list_runs"])
     sweeps = None
     if not args.no_sweeps and world == 1:
-        sweeps = measure_sweeps(dev)
+        sweeps = _section("sweeps", measure_sweeps, dev)
 
     if rank != 0:
         return 0

@@ -354,6 +354,11 @@ def vox_probe_red_or(buf, ops: int, seed: int = 1, stream=None) -> int:
     return int(lib.vox_probe_red_or_ops(int(ops)))
 
 
+def vox_probe_red_or_ops(ops: int) -> int:
+    """The exact number of reductions vox_probe_red_or issues for `ops`."""
+    return int(load().vox_probe_red_or_ops(int(ops)))
+
+
 def vox_host_arena_size(n: int, dims, flags: int, capacity: int) -> int:
     return int(load().vox_host_arena_size(int(n), _dims(dims), int(flags), int(capacity)))
 
