@@ -28,7 +28,6 @@ constexpr size_t kWsAlign = 256;
 constexpr int64_t kMaxDim = int64_t(1) << 21;
 constexpr int64_t kMinPerCta = 2048;          // smallest voxel range given to one CTA
 constexpr int64_t kDefaultWaitNs = 500000000;  // 0.5 s bound on every in-kernel wait
-constexpr size_t kListCounterOffset = 128;    // k_list's chunk counter, in the workspace's ticket region
 
 std::atomic<int64_t> g_stall_tile{-1};
 std::atomic<int64_t> g_wait_ns{kDefaultWaitNs};
@@ -260,17 +259,17 @@ bool uses_bricks(int64_t n, vox_dims dims, size_t ws_bytes, BrickGeom *G, size_t
 int grid_ctas(const void *kernel, int threads, size_t smem);
 
 // The binning passes: persistent grids (SMs x CTAs per SM, no more CTAs than
-// 256-segment groups), threads striding over the segments.
+// the segments fill), warps taking batches of segments.
 template <bool kEuclid, bool kBatched>
 vox_status launch_bin_t(const BinParams &bp, bool scatter, int64_t n, cudaStream_t stream)
 {
     const void *k = scatter ? reinterpret_cast<const void *>(k_bin_scatter<kEuclid, kBatched>)
                             : reinterpret_cast<const void *>(k_bin_count<kEuclid, kBatched>);
-    int grid = grid_ctas(k, 256, 0);
+    int grid = grid_ctas(k, kBinThreads, 0);
     if (grid <= 0) return VOX_ERR_CUDA;
-    grid = static_cast<int>(std::min<int64_t>(grid, (n + 255) / 256));
-    if (scatter) k_bin_scatter<kEuclid, kBatched><<<static_cast<unsigned>(grid), 256, 0, stream>>>(bp);
-    else k_bin_count<kEuclid, kBatched><<<static_cast<unsigned>(grid), 256, 0, stream>>>(bp);
+    grid = static_cast<int>(std::min<int64_t>(grid, (n + kBinWarps * kBinBatch - 1) / (kBinWarps * kBinBatch)));
+    if (scatter) k_bin_scatter<kEuclid, kBatched><<<static_cast<unsigned>(grid), kBinThreads, 0, stream>>>(bp);
+    else k_bin_count<kEuclid, kBatched><<<static_cast<unsigned>(grid), kBinThreads, 0, stream>>>(bp);
     return cudaGetLastError() == cudaSuccess ? VOX_OK : VOX_ERR_CUDA;
 }
 
@@ -404,8 +403,8 @@ vox_status launch_gen_t(const GenParams &p, cudaStream_t stream)
     }
 }
 
-// The list alone by warp slices (k_list): persistent grid, the chunk counter in
-// the workspace's ticket region reset first.
+// The list alone by warp slices (k_list): persistent grid, each warp a
+// contiguous range of slices.
 template <typename PackT>
 vox_status launch_list(const vox_segment *segs, int64_t n, void *list, int64_t capacity, void *ws, int32_t *status,
                        cudaStream_t stream)
@@ -419,13 +418,11 @@ vox_status launch_list(const vox_segment *segs, int64_t n, void *list, int64_t c
     p.list = list;
     p.capacity = capacity;
     p.status = status;
-    p.counter = reinterpret_cast<uint32_t *>(base + kListCounterOffset);
     auto kernel = k_list<PackT>;
     const size_t smem = sizeof(ListWarpSmem<PackT>) * kListWarps;
     if (vox_status e = allow_smem(reinterpret_cast<const void *>(kernel), smem)) return e;
     const int grid = grid_ctas(reinterpret_cast<const void *>(kernel), kListThreads, smem);
     if (grid <= 0) return VOX_ERR_CUDA;
-    if (cudaMemsetAsync(p.counter, 0, sizeof(uint32_t), stream) != cudaSuccess) return VOX_ERR_CUDA;
     kernel<<<static_cast<unsigned>(grid), kListThreads, smem, stream>>>(p);
     return cudaGetLastError() == cudaSuccess ? VOX_OK : VOX_ERR_CUDA;
 }

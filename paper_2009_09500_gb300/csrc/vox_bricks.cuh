@@ -316,46 +316,107 @@ __device__ __forceinline__ void load_record(const int32_t *segs, int64_t s, int3
     r[0] = a.x; r[1] = a.y; r[2] = b.x; r[3] = b.y; r[4] = c.x; r[5] = c.y;
 }
 
-// Binning work loop, shared by the counting and the scattering pass: a
-// persistent grid whose threads take segments s = t, t + T, t + 2T, ... (T the
-// grid's threads) and walk each one's pieces. A thread then sums the work of
-// about n / T segments, so that with lengths of any mix the threads of a warp
-// carry similar totals (one segment per thread would leave a warp waiting for
-// its longest segment). emit(slot, seg, k_lo, len) is called for every piece
-// (runs in one brick cut to at most kPieceMaxLen steps) with its slot in the
-// batch's slot numbering. A segment with an endpoint outside its volume has no
-// pieces (the count kernel reports it).
+// Binning work loop, shared by the counting and the scattering pass (CTAs of
+// kBinThreads threads, persistent grid). Each warp takes batches of kBinBatch
+// consecutive segments, orders each batch by length octave, longest first (a
+// counting sort in the warp's shared memory), and walks the segments in that
+// order, lane l taking the l-th of every 32: the lanes of a warp then walk
+// segments of similar length, so that a warp does not wait for one long
+// segment while its other lanes idle (lengths may span three orders of
+// magnitude). emit(slot, seg, k_lo, len) is called for every piece (runs in one
+// brick cut to at most kPieceMaxLen steps) with its slot in the batch's slot
+// numbering. A segment with an endpoint outside its volume has no pieces (the
+// count kernel reports it).
+constexpr int kBinThreads = 256;
+constexpr int kBinWarps = kBinThreads / 32;
+constexpr int kBinPer = 4;                 // segments per lane and batch
+constexpr int kBinBatch = 32 * kBinPer;    // segments per warp batch
+constexpr int kBinOctaves = 22;            // octaves of N + 1 <= 2^21
+
 template <bool kEuclid, bool kBatched, typename Emit>
 __device__ __forceinline__ void bin_loop(const BinParams &p, Emit &&emit)
 {
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    for (int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; s < p.n; s += stride) {
-        int64_t slot_base;
-        const BrickGeom *Gp = segment_geom<kBatched>(p, s, slot_base);
-        if (Gp == nullptr) continue;
-        int32_t r[6];
-        load_record(p.segs, s, r);
-        if (!endpoints_inside(r, *Gp)) continue;
-        const int32_t rep = static_cast<int32_t>(s) & (Gp->reps - 1);
-        PieceWalker<kEuclid> pw;
-        pw.init(r, *Gp);
-        bool more = true;
-        while (more) {
-            int32_t b, k_lo, len;
-            more = pw.next(b, k_lo, len);
-            while (len > 0) {
-                const int32_t part = min(len, kPieceMaxLen);
-                emit(slot_base + piece_slot(*Gp, b, part, rep), s, k_lo, part);
-                k_lo += part;
-                len -= part;
+    __shared__ int32_t s_recs[kBinWarps][kBinBatch * 6];
+    __shared__ uint8_t s_order[kBinWarps][kBinBatch];
+    __shared__ int32_t s_hist[kBinWarps][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    int32_t *const recs = s_recs[wib];
+    for (int64_t b0 = gw * kBinBatch; b0 < p.n; b0 += nw * kBinBatch) {
+        s_hist[wib][lane] = 0;
+        __syncwarp();
+        // the batch's records, and each segment's rank within its octave (longest first)
+        int32_t oct[kBinPer], rank[kBinPer];
+#pragma unroll
+        for (int i = 0; i < kBinPer; ++i) {
+            const int j = i * 32 + lane;
+            const int64_t s = b0 + j;
+            oct[i] = -1;
+            if (s < p.n) {
+                int32_t r[6];
+                load_record(p.segs, s, r);
+#pragma unroll
+                for (int c = 0; c < 6; ++c) recs[6 * j + c] = r[c];
+                // the octave of N + 1 from unsigned differences: a segment with an
+                // endpoint outside the volume (skipped below) still gets a valid one
+                const uint32_t dx = static_cast<uint32_t>(abs(r[3] - r[0]));
+                const uint32_t dy = static_cast<uint32_t>(abs(r[4] - r[1]));
+                const uint32_t dz = static_cast<uint32_t>(abs(r[5] - r[2]));
+                const uint32_t octave = 31 - __clz(max(dx, max(dy, dz)) | 1u);
+                oct[i] = kBinOctaves - 1 - static_cast<int32_t>(min(octave, static_cast<uint32_t>(kBinOctaves - 1)));
+                rank[i] = atomicAdd(&s_hist[wib][oct[i]], 1);
             }
         }
+        __syncwarp();
+        // octave starts: exclusive scan of the octave counts (one per lane)
+        const int32_t h = s_hist[wib][lane];
+        int32_t inc = h;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const int32_t total = __shfl_sync(0xffffffffu, inc, 31);
+#pragma unroll
+        for (int i = 0; i < kBinPer; ++i) {
+            const int32_t start = __shfl_sync(0xffffffffu, inc - h, max(oct[i], 0));
+            if (oct[i] >= 0) s_order[wib][start + rank[i]] = static_cast<uint8_t>(i * 32 + lane);
+        }
+        __syncwarp();
+#pragma unroll 1
+        for (int i = 0; i < kBinPer; ++i) {
+            const int q = i * 32 + lane;
+            if (q >= total) continue;
+            const int j = s_order[wib][q];
+            const int64_t s = b0 + j;
+            int64_t slot_base;
+            const BrickGeom *Gp = segment_geom<kBatched>(p, s, slot_base);
+            if (Gp == nullptr) continue;
+            const int32_t *r = recs + 6 * j;
+            if (!endpoints_inside(r, *Gp)) continue;
+            const int32_t rep = static_cast<int32_t>(s) & (Gp->reps - 1);
+            PieceWalker<kEuclid> pw;
+            pw.init(r, *Gp);
+            bool more = true;
+            while (more) {
+                int32_t b, k_lo, len;
+                more = pw.next(b, k_lo, len);
+                while (len > 0) {
+                    const int32_t part = min(len, kPieceMaxLen);
+                    emit(slot_base + piece_slot(*Gp, b, part, rep), s, k_lo, part);
+                    k_lo += part;
+                    len -= part;
+                }
+            }
+        }
+        __syncwarp();  // the warp's shared arrays are free for the next batch
     }
 }
 
 // Pieces per slot (persistent grid).
 template <bool kEuclid, bool kBatched = false>
-__global__ void __launch_bounds__(256) k_bin_count(BinParams p)
+__global__ void __launch_bounds__(kBinThreads) k_bin_count(BinParams p)
 {
     // single volume: no status check (this pass may run beside the count + scan
     // that resets the status word); it reads only the segments and the host's
@@ -373,7 +434,7 @@ __global__ void __launch_bounds__(256) k_bin_count(BinParams p)
 // in flight together before their stores, so the returning atomics' latency
 // overlaps.
 template <bool kEuclid, bool kBatched = false>
-__global__ void __launch_bounds__(256) k_bin_scatter(BinParams p)
+__global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinParams p)
 {
     if (ld_volatile_i32(p.status) != 0) return;
     if (__ldg(p.brick_off + p.G.n_slots) > p.capacity) return;  // the volume falls back to atomics
@@ -500,24 +561,45 @@ __device__ __forceinline__ void merge_brick(const uint32_t *bits, const BrickGeo
     }
 }
 
+constexpr int kBrickStage = 2048;  // pieces (and their segment records) staged per round
+
 struct BrickSmem {
     alignas(128) uint32_t bits[kBrickWordsMax];  // also the TMA source tile (128-byte aligned)
+    uint64_t pcs[kBrickStage];                   // staged pieces of the brick
+    int32_t recs[kBrickStage * 6];               // their segments' records
     int32_t origin[3];
-    int32_t next_group;  // next group of 32 pieces of the brick to hand to a warp
+    int32_t next_group;  // next group of 32 staged pieces to hand to a warp
     int64_t brick;
     int64_t first_slot;  // the brick's first slot
     BrickGeom geom;      // batched: the brick's scene geometry
     uint32_t *bmask;     // batched: the scene's volume
 };
 
+// Stage pieces [lo + base, lo + base + m) of the brick and their segment records
+// into shared memory: pieces by coalesced loads, then every thread's records
+// at once (one round of scattered loads for the whole CTA, not one per group).
+__device__ __forceinline__ void stage_pieces(BrickSmem &sm, const BrickParams &p, int64_t from, int32_t m)
+{
+    for (int32_t i = threadIdx.x; i < m; i += kBrickThreads) sm.pcs[i] = __ldg(p.pieces + from + i);
+    __syncthreads();
+    for (int32_t i = threadIdx.x; i < m; i += kBrickThreads) {
+        int32_t r[6];
+        load_record(p.segs, static_cast<int64_t>(sm.pcs[i] & 0xffffffffull), r);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) sm.recs[6 * i + c] = r[c];
+    }
+}
+
 // One CTA per brick (dynamic tickets). The brick's pieces arrive ordered by
-// length class, longest first (the bucket order of the binning), and warps take
-// groups of 32 consecutive pieces from a shared counter: the lanes of a warp
-// walk pieces of similar length and the warps share the brick's work as it
-// comes, longest groups first. Each lane loads its piece and its segment's
-// record, enters the segment at the piece's first step (one division per minor
-// axis) and steps through the piece with the carry recurrence, OR-ing bits into
-// the brick's shared bitmap; the bitmap is then merged into the volume.
+// length class, longest first (the bucket order of the binning); they are
+// staged with their segments' records in shared memory, kBrickStage at a time,
+// and warps take groups of 32 consecutive staged pieces from a shared counter:
+// the lanes of a warp walk pieces of similar length (at most kPieceMaxLen
+// steps) and the warps share the brick's work as it comes, longest groups
+// first, without global-memory waits between groups. Each lane enters its
+// piece's segment at the piece's first step (one division per minor axis) and
+// steps through the piece with the carry recurrence, OR-ing bits into the
+// brick's shared bitmap; the bitmap is then merged into the volume.
 template <bool kEuclid, bool kBatched = false>
 __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, const __grid_constant__ CUtensorMap tmap)
 {
@@ -540,7 +622,6 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
         if (t == 0) {
             const int64_t b = atomicAdd(p.ticket, 1u);
             sm.brick = b;
-            sm.next_group = 0;
             if (b < total_bricks) {
                 int64_t lb = b;  // the brick's index in its volume
                 const BrickGeom *Gt = &p.G;
@@ -575,13 +656,6 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
             continue;
         }
         const int64_t cnt = hi - lo;
-        // the warp's first group: its ticket and piece load go out before the bitmap
-        // clear and its record load after it, so that their latency overlaps the clear
-        int32_t grp = 0;
-        if (lane == 0) grp = atomicAdd(&sm.next_group, 1);
-        grp = __shfl_sync(0xffffffffu, grp, 0);
-        int64_t j = static_cast<int64_t>(grp) * 32 + lane;
-        uint64_t pc = j < cnt ? __ldg(p.pieces + lo + j) : 0ull;
         if (async_store) {  // the previous brick's copy must have read the tile
             if (t == 0) bulk_wait_read_all();
         }
@@ -590,48 +664,50 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
             uint4 *z = reinterpret_cast<uint4 *>(sm.bits);
             for (int q = t; q < G.words / 4; q += kBrickThreads) z[q] = make_uint4(0u, 0u, 0u, 0u);
         }
-        int32_t rec[6] = {0, 0, 0, 0, 0, 0};
-        if (j < cnt) load_record(p.segs, static_cast<int64_t>(pc & 0xffffffffull), rec);
-        __syncthreads();
         // brick-local bit index of (x, y, z): (x - X0) + B0 (y - Y0) + B0 B1 (z - Z0),
         // kept modulo 2^32 while stepping (only the local value is ever used)
         const uint32_t origin = static_cast<uint32_t>(X0) + static_cast<uint32_t>(Y0) * bw +
                                 static_cast<uint32_t>(Z0) * bwh;
+        for (int64_t base = 0; base < cnt; base += kBrickStage) {
+            const int32_t m = static_cast<int32_t>(min(static_cast<int64_t>(kBrickStage), cnt - base));
+            if (t == 0) sm.next_group = 0;
+            stage_pieces(sm, p, lo + base, m);
+            __syncthreads();  // staged (and, the first time, the bitmap cleared)
 #pragma unroll 1
-        while (static_cast<int64_t>(grp) * 32 < cnt) {
-            if (j < cnt) {
-                const int32_t len = static_cast<int32_t>(pc >> 54) + 1;
-                using St = typename std::conditional<kEuclid, EuclidStepper<uint32_t, uint32_t>,
-                                                     Stepper<uint32_t, uint32_t>>::type;
-                St st;
-                st.enter(rec, static_cast<int32_t>((pc >> 32) & 0x3fffffull), bw, bwh);
-                st.L -= origin;
-                // one shared-memory atomic per voxel: cheaper than branching to
-                // merge runs of the same word (measured on both workload shapes);
-                // repeated samples of the Euclidean variant set the same bit again
-                int32_t e = 0;
-                for (; e + 8 <= len; e += 8) {
+            while (true) {
+                int32_t grp = 0;
+                if (lane == 0) grp = atomicAdd(&sm.next_group, 1);
+                grp = __shfl_sync(0xffffffffu, grp, 0);
+                if (grp * 32 >= m) break;
+                const int32_t j = grp * 32 + lane;
+                if (j < m) {
+                    const uint64_t pc = sm.pcs[j];
+                    const int32_t len = static_cast<int32_t>(pc >> 54) + 1;
+                    using St = typename std::conditional<kEuclid, EuclidStepper<uint32_t, uint32_t>,
+                                                         Stepper<uint32_t, uint32_t>>::type;
+                    St st;
+                    st.enter(sm.recs + 6 * j, static_cast<int32_t>((pc >> 32) & 0x3fffffull), bw, bwh);
+                    st.L -= origin;
+                    // one shared-memory atomic per voxel: cheaper than branching to
+                    // merge runs of the same word (measured on both workload shapes);
+                    // repeated samples of the Euclidean variant set the same bit again
+                    int32_t e = 0;
+                    for (; e + 8 <= len; e += 8) {
 #pragma unroll
-                    for (int v = 0; v < 8; ++v) {
+                        for (int v = 0; v < 8; ++v) {
+                            atomicOr(sm.bits + (st.L >> 5), 1u << (st.L & 31u));
+                            st.template step<false, true>();
+                        }
+                    }
+                    for (; e < len; ++e) {
                         atomicOr(sm.bits + (st.L >> 5), 1u << (st.L & 31u));
                         st.template step<false, true>();
                     }
                 }
-                for (; e < len; ++e) {
-                    atomicOr(sm.bits + (st.L >> 5), 1u << (st.L & 31u));
-                    st.template step<false, true>();
-                }
             }
-            __syncwarp();
-            if (lane == 0) grp = atomicAdd(&sm.next_group, 1);
-            grp = __shfl_sync(0xffffffffu, grp, 0);
-            j = static_cast<int64_t>(grp) * 32 + lane;
-            if (j < cnt) {
-                pc = __ldg(p.pieces + lo + j);
-                load_record(p.segs, static_cast<int64_t>(pc & 0xffffffffull), rec);
-            }
+            __syncthreads();  // the stage is free for the next round; the bitmap is complete at the end
         }
-        __syncthreads();
+        if (cnt == 0) __syncthreads();  // the clear is complete
         if (p.bricked) {
             if (t == 0) {
                 fence_proxy_async_smem();
