@@ -28,6 +28,7 @@ constexpr size_t kWsAlign = 256;
 constexpr int64_t kMaxDim = int64_t(1) << 21;
 constexpr int64_t kMinPerCta = 2048;          // smallest voxel range given to one CTA
 constexpr int64_t kDefaultWaitNs = 500000000;  // 0.5 s bound on every in-kernel wait
+constexpr size_t kListCounterOffset = 128;    // k_list's chunk counter, in the workspace's ticket region
 
 std::atomic<int64_t> g_stall_tile{-1};
 std::atomic<int64_t> g_wait_ns{kDefaultWaitNs};
@@ -403,8 +404,8 @@ vox_status launch_gen_t(const GenParams &p, cudaStream_t stream)
     }
 }
 
-// The list alone by warp slices (k_list): persistent grid, each warp a
-// contiguous range of slices.
+// The list alone by warp slices (k_list): persistent grid, the chunk counter in
+// the workspace's ticket region reset first.
 template <typename PackT>
 vox_status launch_list(const vox_segment *segs, int64_t n, void *list, int64_t capacity, void *ws, int32_t *status,
                        cudaStream_t stream)
@@ -418,11 +419,13 @@ vox_status launch_list(const vox_segment *segs, int64_t n, void *list, int64_t c
     p.list = list;
     p.capacity = capacity;
     p.status = status;
+    p.counter = reinterpret_cast<uint32_t *>(base + kListCounterOffset);
     auto kernel = k_list<PackT>;
     const size_t smem = sizeof(ListWarpSmem<PackT>) * kListWarps;
     if (vox_status e = allow_smem(reinterpret_cast<const void *>(kernel), smem)) return e;
     const int grid = grid_ctas(reinterpret_cast<const void *>(kernel), kListThreads, smem);
     if (grid <= 0) return VOX_ERR_CUDA;
+    if (cudaMemsetAsync(p.counter, 0, sizeof(uint32_t), stream) != cudaSuccess) return VOX_ERR_CUDA;
     kernel<<<static_cast<unsigned>(grid), kListThreads, smem, stream>>>(p);
     return cudaGetLastError() == cudaSuccess ? VOX_OK : VOX_ERR_CUDA;
 }

@@ -561,45 +561,24 @@ __device__ __forceinline__ void merge_brick(const uint32_t *bits, const BrickGeo
     }
 }
 
-constexpr int kBrickStage = 2048;  // pieces (and their segment records) staged per round
-
 struct BrickSmem {
     alignas(128) uint32_t bits[kBrickWordsMax];  // also the TMA source tile (128-byte aligned)
-    uint64_t pcs[kBrickStage];                   // staged pieces of the brick
-    int32_t recs[kBrickStage * 6];               // their segments' records
     int32_t origin[3];
-    int32_t next_group;  // next group of 32 staged pieces to hand to a warp
+    int32_t next_group;  // next group of 32 pieces of the brick to hand to a warp
     int64_t brick;
     int64_t first_slot;  // the brick's first slot
     BrickGeom geom;      // batched: the brick's scene geometry
     uint32_t *bmask;     // batched: the scene's volume
 };
 
-// Stage pieces [lo + base, lo + base + m) of the brick and their segment records
-// into shared memory: pieces by coalesced loads, then every thread's records
-// at once (one round of scattered loads for the whole CTA, not one per group).
-__device__ __forceinline__ void stage_pieces(BrickSmem &sm, const BrickParams &p, int64_t from, int32_t m)
-{
-    for (int32_t i = threadIdx.x; i < m; i += kBrickThreads) sm.pcs[i] = __ldg(p.pieces + from + i);
-    __syncthreads();
-    for (int32_t i = threadIdx.x; i < m; i += kBrickThreads) {
-        int32_t r[6];
-        load_record(p.segs, static_cast<int64_t>(sm.pcs[i] & 0xffffffffull), r);
-#pragma unroll
-        for (int c = 0; c < 6; ++c) sm.recs[6 * i + c] = r[c];
-    }
-}
-
 // One CTA per brick (dynamic tickets). The brick's pieces arrive ordered by
-// length class, longest first (the bucket order of the binning); they are
-// staged with their segments' records in shared memory, kBrickStage at a time,
-// and warps take groups of 32 consecutive staged pieces from a shared counter:
-// the lanes of a warp walk pieces of similar length (at most kPieceMaxLen
-// steps) and the warps share the brick's work as it comes, longest groups
-// first, without global-memory waits between groups. Each lane enters its
-// piece's segment at the piece's first step (one division per minor axis) and
-// steps through the piece with the carry recurrence, OR-ing bits into the
-// brick's shared bitmap; the bitmap is then merged into the volume.
+// length class, longest first (the bucket order of the binning), and warps take
+// groups of 32 consecutive pieces from a shared counter: the lanes of a warp
+// walk pieces of similar length and the warps share the brick's work as it
+// comes, longest groups first. Each lane loads its piece and its segment's
+// record, enters the segment at the piece's first step (one division per minor
+// axis) and steps through the piece with the carry recurrence, OR-ing bits into
+// the brick's shared bitmap; the bitmap is then merged into the volume.
 template <bool kEuclid, bool kBatched = false>
 __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, const __grid_constant__ CUtensorMap tmap)
 {
@@ -622,6 +601,7 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
         if (t == 0) {
             const int64_t b = atomicAdd(p.ticket, 1u);
             sm.brick = b;
+            sm.next_group = 0;
             if (b < total_bricks) {
                 int64_t lb = b;  // the brick's index in its volume
                 const BrickGeom *Gt = &p.G;
@@ -656,6 +636,13 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
             continue;
         }
         const int64_t cnt = hi - lo;
+        // the warp's first group: its ticket and piece load go out before the bitmap
+        // clear and its record load after it, so that their latency overlaps the clear
+        int32_t grp = 0;
+        if (lane == 0) grp = atomicAdd(&sm.next_group, 1);
+        grp = __shfl_sync(0xffffffffu, grp, 0);
+        int64_t j = static_cast<int64_t>(grp) * 32 + lane;
+        uint64_t pc = j < cnt ? __ldg(p.pieces + lo + j) : 0ull;
         if (async_store) {  // the previous brick's copy must have read the tile
             if (t == 0) bulk_wait_read_all();
         }
@@ -664,50 +651,48 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
             uint4 *z = reinterpret_cast<uint4 *>(sm.bits);
             for (int q = t; q < G.words / 4; q += kBrickThreads) z[q] = make_uint4(0u, 0u, 0u, 0u);
         }
+        int32_t rec[6] = {0, 0, 0, 0, 0, 0};
+        if (j < cnt) load_record(p.segs, static_cast<int64_t>(pc & 0xffffffffull), rec);
+        __syncthreads();
         // brick-local bit index of (x, y, z): (x - X0) + B0 (y - Y0) + B0 B1 (z - Z0),
         // kept modulo 2^32 while stepping (only the local value is ever used)
         const uint32_t origin = static_cast<uint32_t>(X0) + static_cast<uint32_t>(Y0) * bw +
                                 static_cast<uint32_t>(Z0) * bwh;
-        for (int64_t base = 0; base < cnt; base += kBrickStage) {
-            const int32_t m = static_cast<int32_t>(min(static_cast<int64_t>(kBrickStage), cnt - base));
-            if (t == 0) sm.next_group = 0;
-            stage_pieces(sm, p, lo + base, m);
-            __syncthreads();  // staged (and, the first time, the bitmap cleared)
 #pragma unroll 1
-            while (true) {
-                int32_t grp = 0;
-                if (lane == 0) grp = atomicAdd(&sm.next_group, 1);
-                grp = __shfl_sync(0xffffffffu, grp, 0);
-                if (grp * 32 >= m) break;
-                const int32_t j = grp * 32 + lane;
-                if (j < m) {
-                    const uint64_t pc = sm.pcs[j];
-                    const int32_t len = static_cast<int32_t>(pc >> 54) + 1;
-                    using St = typename std::conditional<kEuclid, EuclidStepper<uint32_t, uint32_t>,
-                                                         Stepper<uint32_t, uint32_t>>::type;
-                    St st;
-                    st.enter(sm.recs + 6 * j, static_cast<int32_t>((pc >> 32) & 0x3fffffull), bw, bwh);
-                    st.L -= origin;
-                    // one shared-memory atomic per voxel: cheaper than branching to
-                    // merge runs of the same word (measured on both workload shapes);
-                    // repeated samples of the Euclidean variant set the same bit again
-                    int32_t e = 0;
-                    for (; e + 8 <= len; e += 8) {
+        while (static_cast<int64_t>(grp) * 32 < cnt) {
+            if (j < cnt) {
+                const int32_t len = static_cast<int32_t>(pc >> 54) + 1;
+                using St = typename std::conditional<kEuclid, EuclidStepper<uint32_t, uint32_t>,
+                                                     Stepper<uint32_t, uint32_t>>::type;
+                St st;
+                st.enter(rec, static_cast<int32_t>((pc >> 32) & 0x3fffffull), bw, bwh);
+                st.L -= origin;
+                // one shared-memory atomic per voxel: cheaper than branching to
+                // merge runs of the same word (measured on both workload shapes);
+                // repeated samples of the Euclidean variant set the same bit again
+                int32_t e = 0;
+                for (; e + 8 <= len; e += 8) {
 #pragma unroll
-                        for (int v = 0; v < 8; ++v) {
-                            atomicOr(sm.bits + (st.L >> 5), 1u << (st.L & 31u));
-                            st.template step<false, true>();
-                        }
-                    }
-                    for (; e < len; ++e) {
+                    for (int v = 0; v < 8; ++v) {
                         atomicOr(sm.bits + (st.L >> 5), 1u << (st.L & 31u));
                         st.template step<false, true>();
                     }
                 }
+                for (; e < len; ++e) {
+                    atomicOr(sm.bits + (st.L >> 5), 1u << (st.L & 31u));
+                    st.template step<false, true>();
+                }
             }
-            __syncthreads();  // the stage is free for the next round; the bitmap is complete at the end
+            __syncwarp();
+            if (lane == 0) grp = atomicAdd(&sm.next_group, 1);
+            grp = __shfl_sync(0xffffffffu, grp, 0);
+            j = static_cast<int64_t>(grp) * 32 + lane;
+            if (j < cnt) {
+                pc = __ldg(p.pieces + lo + j);
+                load_record(p.segs, static_cast<int64_t>(pc & 0xffffffffull), rec);
+            }
         }
-        if (cnt == 0) __syncthreads();  // the clear is complete
+        __syncthreads();
         if (p.bricked) {
             if (t == 0) {
                 fence_proxy_async_smem();

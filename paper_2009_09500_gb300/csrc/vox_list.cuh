@@ -12,14 +12,12 @@
 // minimum for 256 bytes). The finished slice leaves with one TMA bulk copy from
 // shared to global memory (cp.async.bulk), so the SM issues no load/store
 // instructions for the write-out and no CTA-wide barrier: each warp runs on its
-// own, on a contiguous range of whole slices (equal voxel counts per warp: the
-// work per voxel hardly varies), found once by a search in the offsets.
+// own, taking chunks of slices from a global work counter (one atomic per chunk).
 //
 // Segment records and offsets are staged per warp in windows of 32 segments
-// (plain coalesced loads into the warp's shared memory) and kept while the next
-// slice still starts inside the window; a slice that spans more segments is
-// processed in several windows, each lane keeping its stepping state across
-// them.
+// (plain coalesced loads into the warp's shared memory); a slice that spans more
+// segments is processed in several windows, each lane keeping its stepping state
+// across them.
 #pragma once
 
 #include <cstdint>
@@ -36,6 +34,7 @@ constexpr int kListSlice = 32 * kListRun;      // voxels per warp slice (1056, a
 constexpr int kListWarps = 4;                  // warps per CTA
 constexpr int kListThreads = 32 * kListWarps;
 constexpr int kListWin = 32;                   // segments per staged window
+constexpr int kListChunkSlices = 4;            // slices per fetch from the work counter
 static_assert(kListSlice % 4 == 0, "slices must keep 16-byte aligned list addresses");
 
 struct ListParams {
@@ -45,6 +44,7 @@ struct ListParams {
     void *list;              // uint32 or uint64 list, 16-byte aligned
     int64_t capacity;
     int32_t *status;
+    uint32_t *counter;       // chunk counter, zeroed before the launch
 };
 
 template <typename PackT>
@@ -111,111 +111,106 @@ __global__ void __launch_bounds__(kListThreads) k_list(ListParams p)
     if (!s_go) return;
     const int64_t V = s_V;
     PackT *const list = static_cast<PackT *>(p.list);
+    constexpr int64_t kChunk = static_cast<int64_t>(kListChunkSlices) * kListSlice;
     bool pending = false;  // lane 0: a bulk store may still be reading this warp's stage
 
-    // this warp's slices: [sl0, sl1) of the V / kListSlice (rounded up) slices
-    const int64_t n_slices = (V + kListSlice - 1) / kListSlice;
-    const int64_t n_warps = static_cast<int64_t>(gridDim.x) * kListWarps;
-    const int64_t wid = static_cast<int64_t>(blockIdx.x) * kListWarps + warp;
-    const int64_t sl0 = n_slices * wid / n_warps, sl1 = n_slices * (wid + 1) / n_warps;
-    if (sl0 >= sl1) return;
-    const int64_t g_end = min64(sl1 * kListSlice, V);
-    int64_t s = warp_find_segment(p.offsets, p.n, sl0 * kListSlice, lane);
-    int64_t ws = -1;       // first segment of the staged window (-1: none)
-    int32_t wcnt = 0;      // segments in it
-    for (int64_t g = sl0 * kListSlice; g < g_end; g += kListSlice) {
-        const int32_t len = static_cast<int32_t>(min64(kListSlice, g_end - g));
-        const int32_t my0 = kListRun * lane;
-        const int32_t rlen = max(0, min(kListRun, len - my0));
-        if (lane == 0 && pending) bulk_wait_read_all();  // the stage is free again
-        __syncwarp();
+    while (true) {
+        uint32_t c = 0;
+        if (lane == 0) c = atomicAdd(p.counter, 1u);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        const int64_t g_begin = static_cast<int64_t>(c) * kChunk;
+        if (g_begin >= V) break;
+        const int64_t g_end = min64(g_begin + kChunk, V);
+        int64_t s = warp_find_segment(p.offsets, p.n, g_begin, lane);
+        for (int64_t g = g_begin; g < g_end; g += kListSlice) {
+            const int32_t len = static_cast<int32_t>(min64(kListSlice, g_end - g));
+            const int32_t my0 = kListRun * lane;
+            const int32_t rlen = max(0, min(kListRun, len - my0));
+            if (lane == 0 && pending) bulk_wait_read_all();  // the stage is free again
+            __syncwarp();
 
-        Stepper<PackT, uint32_t> st;
-        int32_t done = 0;
-        int64_t cur = -1;   // the segment being walked (-1: not found yet)
-        int32_t kin = 0;    // step at which to enter it
-        bool live = false;  // stepping state valid for cur
-        bool ended = false; // the last voxel written ended its segment
-        // keep the staged window while the slice starts inside it
-        bool staged = ws >= 0 && s >= ws && s < ws + wcnt;
-        if (!staged) ws = s;
-        while (__any_sync(0xffffffffu, done < rlen)) {
-            if (!staged) {
-                wcnt = static_cast<int32_t>(min64(kListWin, p.n - ws));
+            Stepper<PackT, uint32_t> st;
+            int32_t done = 0;
+            int64_t cur = -1;   // the segment being walked (-1: not found yet)
+            int32_t kin = 0;    // step at which to enter it
+            bool live = false;  // stepping state valid for cur
+            bool ended = false; // the last voxel written ended its segment
+            int64_t ws = s;     // first segment of the window
+            while (__any_sync(0xffffffffu, done < rlen)) {
+                const int32_t wcnt = static_cast<int32_t>(min64(kListWin, p.n - ws));
                 __syncwarp();  // every lane is done with the previous window
-                const int64_t sj = ws + lane;
-                if (lane < wcnt) {
-                    const int2 *r = reinterpret_cast<const int2 *>(p.segs + 6 * sj);
-                    const int2 a = __ldg(r), b = __ldg(r + 1), e = __ldg(r + 2);
-                    int32_t *d = sm.recs + 6 * lane;
-                    d[0] = a.x; d[1] = a.y; d[2] = b.x; d[3] = b.y; d[4] = e.x; d[5] = e.y;
+                {
+                    const int64_t sj = ws + lane;
+                    if (lane < wcnt) {
+                        const int2 *r = reinterpret_cast<const int2 *>(p.segs + 6 * sj);
+                        const int2 a = __ldg(r), b = __ldg(r + 1), e = __ldg(r + 2);
+                        int32_t *d = sm.recs + 6 * lane;
+                        d[0] = a.x; d[1] = a.y; d[2] = b.x; d[3] = b.y; d[4] = e.x; d[5] = e.y;
+                    }
+                    if (lane <= wcnt) sm.offs[lane] = __ldg(p.offsets + sj);
+                    if (lane == 0 && wcnt == kListWin) sm.offs[kListWin] = __ldg(p.offsets + ws + kListWin);
                 }
-                if (lane <= wcnt) sm.offs[lane] = __ldg(p.offsets + sj);
-                if (lane == 0 && wcnt == kListWin) sm.offs[kListWin] = __ldg(p.offsets + ws + kListWin);
                 __syncwarp();
-            }
-            staged = false;  // a further round needs the next window
-            if (done < rlen) {
-                if (cur < 0) {  // the segment of the run's first voxel, if in this window
-                    const int64_t r = g + my0;
-                    if (r < sm.offs[wcnt]) {
-                        const int32_t j = find_in_window32(sm.offs, wcnt, r);
-                        cur = ws + j;
-                        kin = static_cast<int32_t>(r - sm.offs[j]);
+                if (done < rlen) {
+                    if (cur < 0) {  // the segment of the run's first voxel, if in this window
+                        const int64_t r = g + my0;
+                        if (r < sm.offs[wcnt]) {
+                            const int32_t j = find_in_window32(sm.offs, wcnt, r);
+                            cur = ws + j;
+                            kin = static_cast<int32_t>(r - sm.offs[j]);
+                        }
                     }
-                }
-                PackT *o = sm.stage + my0 + done;
-                while (cur >= 0 && done < rlen && cur < ws + wcnt) {
-                    if (!live) {
-                        st.enter(sm.recs + 6 * static_cast<int32_t>(cur - ws), kin, 0u, 0u);
-                        live = true;
-                    }
-                    const int32_t m = min(st.left + 1, rlen - done);
-                    ended = (m == st.left + 1);
-                    int32_t e = 0;
-                    for (; e + 4 <= m; e += 4) {
+                    PackT *o = sm.stage + my0 + done;
+                    while (cur >= 0 && done < rlen && cur < ws + wcnt) {
+                        if (!live) {
+                            st.enter(sm.recs + 6 * static_cast<int32_t>(cur - ws), kin, 0u, 0u);
+                            live = true;
+                        }
+                        const int32_t m = min(st.left + 1, rlen - done);
+                        ended = (m == st.left + 1);
+                        int32_t e = 0;
+                        for (; e + 4 <= m; e += 4) {
 #pragma unroll
-                        for (int v = 0; v < 4; ++v) {
-                            o[v] = st.P;
+                            for (int v = 0; v < 4; ++v) {
+                                o[v] = st.P;
+                                st.template step<true, false>();
+                            }
+                            o += 4;
+                        }
+                        for (; e < m; ++e) {
+                            *o++ = st.P;
                             st.template step<true, false>();
                         }
-                        o += 4;
-                    }
-                    for (; e < m; ++e) {
-                        *o++ = st.P;
-                        st.template step<true, false>();
-                    }
-                    done += m;
-                    if (done < rlen) {  // the run goes on in the next segment
-                        ++cur;
-                        kin = 0;
-                        live = false;
+                        done += m;
+                        if (done < rlen) {  // the run goes on in the next segment
+                            ++cur;
+                            kin = 0;
+                            live = false;
+                        }
                     }
                 }
-            }
-            if (__any_sync(0xffffffffu, done < rlen)) {
                 ws += wcnt;
                 if (wcnt == 0) break;  // unreachable for a consistent scan; keeps the loop finite
             }
-        }
-        // the next slice starts in the segment of this slice's last voxel, or
-        // the next one if that voxel ended its segment
-        const int last = (len - 1) / kListRun;
-        const int64_t cur_last = __shfl_sync(0xffffffffu, cur, last);
-        const bool ended_last = __shfl_sync(0xffffffffu, ended ? 1 : 0, last) != 0;
-        s = cur_last + (ended_last ? 1 : 0);
+            // the next slice starts in the segment of this slice's last voxel, or
+            // the next one if that voxel ended its segment
+            const int last = (len - 1) / kListRun;
+            const int64_t cur_last = __shfl_sync(0xffffffffu, cur, last);
+            const bool ended_last = __shfl_sync(0xffffffffu, ended ? 1 : 0, last) != 0;
+            s = cur_last + (ended_last ? 1 : 0);
 
-        // write-out: the 16-byte part by one bulk copy, a ragged end (only at
-        // the end of the list) by plain stores
-        fence_proxy_async_smem();  // this lane's stage writes, visible to the bulk-copy unit
-        __syncwarp();
-        const uint32_t bytes = (static_cast<uint32_t>(len) * sizeof(PackT)) & ~15u;
-        if (lane == 0 && bytes) {
-            bulk_store_1d(list + g, sm.stage, bytes);
-            pending = true;
+            // write-out: the 16-byte part by one bulk copy, a ragged end (only at
+            // the end of the list) by plain stores
+            fence_proxy_async_smem();  // this lane's stage writes, visible to the bulk-copy unit
+            __syncwarp();
+            const uint32_t bytes = (static_cast<uint32_t>(len) * sizeof(PackT)) & ~15u;
+            if (lane == 0 && bytes) {
+                bulk_store_1d(list + g, sm.stage, bytes);
+                pending = true;
+            }
+            const int32_t tail0 = static_cast<int32_t>(bytes / sizeof(PackT));
+            for (int32_t e = tail0 + lane; e < len; e += 32) list[g + e] = sm.stage[e];
         }
-        const int32_t tail0 = static_cast<int32_t>(bytes / sizeof(PackT));
-        for (int32_t e = tail0 + lane; e < len; e += 32) list[g + e] = sm.stage[e];
     }
     if (lane == 0 && pending) bulk_wait_all();  // copies complete before the CTA's memory goes
 }
