@@ -931,6 +931,46 @@ def measure_atomics(dev, stream, flush, reps: int, big: bool = True) -> dict:
                     "L2 flushed between calls"}
 
 
+def measure_phase(phase: str, n: int, edge: int, steps: int, dev, stream, flush) -> dict:
+    """One phase of a log-uniform batch of n segments in an edge^3 volume (the
+    headline workload's shape at a size a profiler can replay): the list64
+    alone or the fresh volume alone, `steps` launches after one count, with the
+    launch tuning in force (--tuning)."""
+    import torch
+
+    from paper_2009_09500_gb300 import vox, workloads
+
+    w = workloads.config3(n=n, edge=edge)
+    segs = torch.from_numpy(w.segs).to(dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws = torch.empty(vox.vox_workspace_size_volume(n, w.dims, 0), dtype=torch.uint8, device=dev)
+    V, P = vox.vox_plan(segs, w.dims, ws, st)
+    ws = torch.empty(vox.vox_workspace_size_volume(n, w.dims, P), dtype=torch.uint8, device=dev)
+    vox.vox_count(segs, w.dims, ws, st, None, None, stream)
+    if phase == "list":
+        out = torch.empty(V, dtype=torch.int64, device=dev)
+        run = lambda: vox.vox_generate_from_scan(segs, w.dims, ws, st, out, None, vox.OUT_LIST64, stream, capacity=V)
+        nbytes = 24 * n + 8 * V
+    else:
+        out = torch.empty(vox.vox_mask_words(w.dims), dtype=torch.int32, device=dev)
+        run = lambda: vox.vox_generate_from_scan(segs, w.dims, ws, st, None, out, vox.OUT_BITMASK | vox.OUT_FRESH,
+                                                 stream)
+        nbytes = 24 * n + 4 * out.numel()
+    ts = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        run()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    if int(st.item()) != 0:
+        raise RuntimeError(vox.strerror(int(st.item())))
+    return {"phase": phase, "segments": n, "edge": edge, "voxels": V, "pieces": P, "ms": ts,
+            "algorithmic_bytes": nbytes, "tuning": vox.vox_get_tuning()}
+
+
 def _section(name, fn, *a, **kw):
     """An auxiliary measurement: its result, or the error it raised (so that one
     failing side measurement does not lose the headline line)."""
@@ -963,6 +1003,13 @@ def run_ours(args):
     if args.only == "atomics":  # one section alone (e.g. under a profiler)
         print(json.dumps({"atomic_volume": measure_atomics(dev, stream, flush, min(args.steps, 10),
                                                            big=not args.no_big_probe)}), flush=True)
+        return 0
+    if args.only and args.tuning:
+        knobs = [int(x) for x in args.tuning.split(",")] + [0]
+        vox.vox_set_tuning(*knobs[:4])
+    if args.only in ("list", "volume"):  # one phase of a smaller log-uniform batch (profiler runs)
+        print(json.dumps(measure_phase(args.only, args.segments, args.edge, args.steps, dev, stream, flush)),
+              flush=True)
         return 0
 
     # headline: each rank voxelizes its own arbitrary-length batch (weak scaling)
@@ -1065,7 +1112,10 @@ def main():
     ap.add_argument("--no-config2", action="store_true")
     ap.add_argument("--no-latency", action="store_true")
     ap.add_argument("--no-atomics", action="store_true")
-    ap.add_argument("--only", choices=["atomics"], default=None, help="run one section alone and print it")
+    ap.add_argument("--only", choices=["atomics", "list", "volume"], default=None,
+                    help="run one section alone and print it (list / volume: one phase of a smaller log-uniform batch)")
+    ap.add_argument("--segments", type=int, default=1 << 19, help="--only list/volume: segments")
+    ap.add_argument("--edge", type=int, default=2048, help="--only list/volume: volume edge")
     ap.add_argument("--no-big-probe", action="store_true", help="atomics: skip the 8 GiB red.or probe")
     ap.add_argument("--tuning", default="", help="run_len,volume_path,ctas_per_sm[,list_runs]: use this launch tuning")
     ap.add_argument("--serve-seconds", type=float, default=1.0)

@@ -561,24 +561,63 @@ __device__ __forceinline__ void merge_brick(const uint32_t *bits, const BrickGeo
     }
 }
 
-struct BrickSmem {
-    alignas(128) uint32_t bits[kBrickWordsMax];  // also the TMA source tile (128-byte aligned)
-    int32_t origin[3];
-    int32_t next_group;  // next group of 32 pieces of the brick to hand to a warp
+// A brick taken from the ticket counter: its index, its pieces [lo, hi) and its
+// origin (and, in a batch, its scene's geometry and volume).
+struct BrickInfo {
     int64_t brick;
-    int64_t first_slot;  // the brick's first slot
+    int64_t lo, hi;
+    int32_t origin[3];
     BrickGeom geom;      // batched: the brick's scene geometry
     uint32_t *bmask;     // batched: the scene's volume
 };
 
-// One CTA per brick (dynamic tickets). The brick's pieces arrive ordered by
-// length class, longest first (the bucket order of the binning), and warps take
-// groups of 32 consecutive pieces from a shared counter: the lanes of a warp
-// walk pieces of similar length and the warps share the brick's work as it
-// comes, longest groups first. Each lane loads its piece and its segment's
-// record, enters the segment at the piece's first step (one division per minor
-// axis) and steps through the piece with the carry recurrence, OR-ing bits into
-// the brick's shared bitmap; the bitmap is then merged into the volume.
+struct BrickSmem {
+    alignas(128) uint32_t bits[kBrickWordsMax];  // also the TMA source tile (128-byte aligned)
+    BrickInfo info[2];   // the brick in hand and the next one (taken one ahead)
+    int32_t next_group;  // next group of 32 pieces of the brick to hand to a warp
+};
+
+// Take the next brick ticket and describe the brick (one thread).
+template <bool kBatched>
+__device__ __forceinline__ void take_brick(const BrickParams &p, bool overflow, BrickInfo &I)
+{
+    const int64_t b = atomicAdd(p.ticket, 1u);
+    I.brick = b;
+    if (b >= p.G.n_bricks) return;
+    int64_t lb = b;  // the brick's index in its volume
+    const BrickGeom *Gt = &p.G;
+    int64_t first_slot;
+    if constexpr (kBatched) {  // the brick's scene and its geometry
+        const int32_t k = __ldg(p.brick_scene + b);
+        I.geom = p.sb[k].G;
+        I.bmask = p.sb[k].mask;
+        lb = b - p.sb[k].brick_base;
+        first_slot = p.sb[k].slot_base + lb * kPieceClasses;
+        Gt = &I.geom;
+    } else {
+        first_slot = b * kPieceClasses * p.G.reps;
+    }
+    const int64_t rest = lb / Gt->nb[0];
+    I.origin[0] = static_cast<int32_t>(lb - rest * Gt->nb[0]) * Gt->B[0];
+    I.origin[1] = static_cast<int32_t>(rest % Gt->nb[1]) * Gt->B[1];
+    I.origin[2] = static_cast<int32_t>(rest / Gt->nb[1]) * Gt->B[2];
+    const int64_t slots_per_brick = static_cast<int64_t>(kPieceClasses) * Gt->reps;
+    I.lo = overflow ? 0 : __ldg(p.brick_off + first_slot);
+    I.hi = overflow ? 0 : __ldg(p.brick_off + first_slot + slots_per_brick);
+}
+
+// One CTA per brick (dynamic tickets, taken one brick ahead). The brick's
+// pieces arrive ordered by length class, longest first (the bucket order of the
+// binning). Group w of 32 consecutive pieces goes to warp w, further groups to
+// the warps that ask a shared counter first: the lanes of a warp walk pieces of
+// similar length (at most kPieceMaxLen steps), longest groups first. A warp's
+// first group of the next brick is loaded while it walks the current brick
+// (its pieces during the walk, their segment records after it), so that, with
+// about as many groups per brick as warps, most groups start without waiting
+// for global memory. Each lane enters its piece's segment at the piece's first
+// step (one division per minor axis) and steps through the piece with the
+// carry recurrence, OR-ing bits into the brick's shared bitmap; the bitmap is
+// then merged into the volume.
 template <bool kEuclid, bool kBatched = false>
 __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, const __grid_constant__ CUtensorMap tmap)
 {
@@ -586,6 +625,7 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
     BrickSmem &sm = *reinterpret_cast<BrickSmem *>(brick_smem_raw);
     const int t = threadIdx.x;
     const int lane = t & 31;
+    const int warp = t >> 5;
     if (ld_volatile_i32(p.status) != 0) return;
     // pieces that did not fit: the gated atomics pass ORs the voxels in (after a
     // fresh volume has been cleared here, brick by brick)
@@ -597,62 +637,54 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
     if (overflow && !p.fresh) return;
     const bool async_store = p.use_tma || p.bricked;  // the bitmap leaves by the bulk-copy unit
     const int64_t total_bricks = p.G.n_bricks;
+    using St = typename std::conditional<kEuclid, EuclidStepper<uint32_t, uint32_t>, Stepper<uint32_t, uint32_t>>::type;
+    // this warp's first group of the brick in hand, when loaded ahead
+    bool have_pref = false;
+    uint64_t pc_pref = 0;
+    int32_t rec_pref[6] = {0, 0, 0, 0, 0, 0};
+    int cur = 0;
+    if (t == 0) take_brick<kBatched>(p, overflow, sm.info[0]);
     while (true) {
-        if (t == 0) {
-            const int64_t b = atomicAdd(p.ticket, 1u);
-            sm.brick = b;
-            sm.next_group = 0;
-            if (b < total_bricks) {
-                int64_t lb = b;  // the brick's index in its volume
-                const BrickGeom *Gt = &p.G;
-                if constexpr (kBatched) {  // the brick's scene and its geometry
-                    const int32_t k = __ldg(p.brick_scene + b);
-                    sm.geom = p.sb[k].G;
-                    sm.bmask = p.sb[k].mask;
-                    lb = b - p.sb[k].brick_base;
-                    sm.first_slot = p.sb[k].slot_base + lb * kPieceClasses;
-                    Gt = &sm.geom;
-                } else {
-                    sm.first_slot = b * kPieceClasses * p.G.reps;
-                }
-                const int64_t rest = lb / Gt->nb[0];
-                sm.origin[0] = static_cast<int32_t>(lb - rest * Gt->nb[0]) * Gt->B[0];
-                sm.origin[1] = static_cast<int32_t>(rest % Gt->nb[1]) * Gt->B[1];
-                sm.origin[2] = static_cast<int32_t>(rest / Gt->nb[1]) * Gt->B[2];
-            }
-        }
+        if (t == 0) take_brick<kBatched>(p, overflow, sm.info[cur ^ 1]);
         __syncthreads();
-        const int64_t b = sm.brick;
+        const BrickInfo &I = sm.info[cur];
+        const BrickInfo &NI = sm.info[cur ^ 1];
+        const int64_t b = I.brick;
         if (b >= total_bricks) break;
-        const BrickGeom &G = kBatched ? sm.geom : p.G;
-        const int32_t X0 = sm.origin[0], Y0 = sm.origin[1], Z0 = sm.origin[2];
+        const BrickGeom &G = kBatched ? I.geom : p.G;
+        const int32_t X0 = I.origin[0], Y0 = I.origin[1], Z0 = I.origin[2];
         const uint32_t bw = static_cast<uint32_t>(G.B[0]);
         const uint32_t bwh = static_cast<uint32_t>(G.B[0]) * static_cast<uint32_t>(G.B[1]);
-        const int64_t slots_per_brick = static_cast<int64_t>(kPieceClasses) * G.reps;
-        const int64_t lo = overflow ? 0 : __ldg(p.brick_off + sm.first_slot);
-        const int64_t hi = overflow ? 0 : __ldg(p.brick_off + sm.first_slot + slots_per_brick);
-        if (lo == hi && !p.fresh) {
-            __syncthreads();  // everyone has read the ticket slot before it is rewritten
+        const int64_t lo = I.lo, cnt = I.hi - I.lo;
+        const bool next_ok = NI.brick < total_bricks;
+        const int64_t lo_n = NI.lo, cnt_n = next_ok ? NI.hi - NI.lo : 0;
+        if (cnt == 0 && !p.fresh) {
+            have_pref = false;
+            cur ^= 1;
+            __syncthreads();  // everyone has read the brick records before they are rewritten
             continue;
         }
-        const int64_t cnt = hi - lo;
-        // the warp's first group: its ticket and piece load go out before the bitmap
-        // clear and its record load after it, so that their latency overlaps the clear
-        int32_t grp = 0;
-        if (lane == 0) grp = atomicAdd(&sm.next_group, 1);
-        grp = __shfl_sync(0xffffffffu, grp, 0);
+        // the warp's first group (group `warp`): loaded ahead, or its pieces now
+        // (their records after the clear, so that the latency overlaps it)
+        int32_t grp = warp;
         int64_t j = static_cast<int64_t>(grp) * 32 + lane;
-        uint64_t pc = j < cnt ? __ldg(p.pieces + lo + j) : 0ull;
-        if (async_store) {  // the previous brick's copy must have read the tile
-            if (t == 0) bulk_wait_read_all();
+        uint64_t pc = have_pref ? pc_pref : (j < cnt ? __ldg(p.pieces + lo + j) : 0ull);
+        int32_t rec[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) rec[c] = rec_pref[c];
+        // the next brick's first group for this warp: its pieces now, consumed after the walk
+        const int64_t jn = static_cast<int64_t>(warp) * 32 + lane;
+        const uint64_t pc_n = jn < cnt_n ? __ldg(p.pieces + lo_n + jn) : 0ull;
+        if (t == 0) {
+            sm.next_group = kBrickThreads / 32;  // groups beyond the first round, on demand
+            if (async_store) bulk_wait_read_all();  // the previous brick's copy must have read the tile
         }
         __syncthreads();
         {  // words is a multiple of 4 (bxw * B1 * B2 with B1 * B2 >= 8)
             uint4 *z = reinterpret_cast<uint4 *>(sm.bits);
             for (int q = t; q < G.words / 4; q += kBrickThreads) z[q] = make_uint4(0u, 0u, 0u, 0u);
         }
-        int32_t rec[6] = {0, 0, 0, 0, 0, 0};
-        if (j < cnt) load_record(p.segs, static_cast<int64_t>(pc & 0xffffffffull), rec);
+        if (!have_pref && j < cnt) load_record(p.segs, static_cast<int64_t>(pc & 0xffffffffull), rec);
         __syncthreads();
         // brick-local bit index of (x, y, z): (x - X0) + B0 (y - Y0) + B0 B1 (z - Z0),
         // kept modulo 2^32 while stepping (only the local value is ever used)
@@ -662,8 +694,6 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
         while (static_cast<int64_t>(grp) * 32 < cnt) {
             if (j < cnt) {
                 const int32_t len = static_cast<int32_t>(pc >> 54) + 1;
-                using St = typename std::conditional<kEuclid, EuclidStepper<uint32_t, uint32_t>,
-                                                     Stepper<uint32_t, uint32_t>>::type;
                 St st;
                 st.enter(rec, static_cast<int32_t>((pc >> 32) & 0x3fffffull), bw, bwh);
                 st.L -= origin;
@@ -692,6 +722,10 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
                 load_record(p.segs, static_cast<int64_t>(pc & 0xffffffffull), rec);
             }
         }
+        // the next brick's first group: its pieces have arrived, now their records
+        have_pref = next_ok;
+        pc_pref = pc_n;
+        if (jn < cnt_n) load_record(p.segs, static_cast<int64_t>(pc_n & 0xffffffffull), rec_pref);
         __syncthreads();
         if (p.bricked) {
             if (t == 0) {
@@ -705,10 +739,11 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
                 else tma_reduce_or_3d(&tmap, sm.bits, X0 / 32, Y0, Z0);
             }
         } else {
-            uint32_t *const mask = kBatched ? sm.bmask : p.mask;
+            uint32_t *const mask = kBatched ? I.bmask : p.mask;
             if (mask != nullptr) merge_brick(sm.bits, G, X0, Y0, Z0, mask, p.fresh != 0);
             __syncthreads();
         }
+        cur ^= 1;
     }
     if (async_store && t == 0) bulk_wait_all();  // copies complete before the CTA's memory goes
 }
