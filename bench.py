@@ -361,6 +361,12 @@ def aggregate_ranks(ms_local: float, voxels_local: int, world: int, device):
     return ms_max, total, total / (ms_max / 1000.0)
 
 
+def vox_tuning_list_runs() -> int:
+    from paper_2009_09500_gb300 import vox
+
+    return int(vox.vox_get_tuning()["list_runs"])
+
+
 # ------------------------------------------------------------ one scene's step
 class SceneBench:
     """One scene's whole step (count + scan, the list, a fresh volume by bricks)
@@ -481,7 +487,8 @@ class SceneBench:
         peaks, peak_kind = _measured_peaks()
         hbm = float(peaks["hbm_gbs"])
         n = self.w.n
-        lname = "k_generate<list64>" if self.elem == 8 else "k_generate<list32>"
+        kind = "k_list" if vox_tuning_list_runs() == 2 else "k_generate"
+        lname = f"{kind}<list64>" if self.elem == 8 else f"{kind}<list32>"
         list_mean, vol_mean = float(np.mean(t["list_ms"])), float(np.mean(t["vol_ms"]))
         list_bytes = 24 * n + self.elem * self.V
         vol_bytes = 24 * n + 4 * self.words
@@ -1083,9 +1090,10 @@ def run_ours(args):
         "roofline": roofline, "roofline_other": roofline_other, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all,
         "e2e": e2e, "clocks": clocks,
         "gpu_launches": 7 * args.steps,
-        "gpu_launches_note": "graph-timed region, per step: k_scan<true>, k_bin_count, k_generate (list64), "
-                             "k_scan<false>, k_bin_scatter, k_brick_volume, k_generate (gated volume fallback; exits "
-                             "at once); the eager per-phase region launches the same 7 per step",
+        "gpu_launches_note": "graph-timed region, per step: k_scan<true>, k_bin_count, the list kernel (k_list with "
+                             "list_runs 2, else k_generate), k_scan<false>, k_bin_scatter, k_brick_volume, "
+                             "k_generate (gated volume fallback; exits at once); the eager per-phase region launches "
+                             "the same 7 per step",
         "batched_vs_plain": batched, "config2_fixed_length": cfg2, "config1_latency": latency,
         "serving": served, "bricked_volume": bricked, "sweeps": sweeps, "atomic_volume": atomics,
     }

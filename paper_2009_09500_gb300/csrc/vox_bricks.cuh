@@ -573,7 +573,7 @@ struct BrickInfo {
 
 struct BrickSmem {
     alignas(128) uint32_t bits[kBrickWordsMax];  // also the TMA source tile (128-byte aligned)
-    BrickInfo info[2];   // the brick in hand and the next one (taken one ahead)
+    BrickInfo info[3];   // a ring: the brick in hand, the next one, and the one after (taken ahead)
     int32_t next_group;  // next group of 32 pieces of the brick to hand to a warp
 };
 
@@ -606,7 +606,8 @@ __device__ __forceinline__ void take_brick(const BrickParams &p, bool overflow, 
     I.hi = overflow ? 0 : __ldg(p.brick_off + first_slot + slots_per_brick);
 }
 
-// One CTA per brick (dynamic tickets, taken one brick ahead). The brick's
+// One CTA per brick (dynamic tickets, taken two bricks ahead by the last warp
+// while the others walk, so that no barrier waits for a ticket). The brick's
 // pieces arrive ordered by length class, longest first (the bucket order of the
 // binning). Group w of 32 consecutive pieces goes to warp w, further groups to
 // the warps that ask a shared counter first: the lanes of a warp walk pieces of
@@ -642,13 +643,17 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
     bool have_pref = false;
     uint64_t pc_pref = 0;
     int32_t rec_pref[6] = {0, 0, 0, 0, 0, 0};
-    int cur = 0;
-    if (t == 0) take_brick<kBatched>(p, overflow, sm.info[0]);
+    // ring positions of the brick in hand, the next one and the one after
+    int cur = 0, nxt = 1, aft = 2;
+    const bool taker = t == kBrickThreads - 32;  // lane 0 of the last warp takes the tickets
+    if (taker) {
+        take_brick<kBatched>(p, overflow, sm.info[0]);
+        take_brick<kBatched>(p, overflow, sm.info[1]);
+    }
     while (true) {
-        if (t == 0) take_brick<kBatched>(p, overflow, sm.info[cur ^ 1]);
         __syncthreads();
         const BrickInfo &I = sm.info[cur];
-        const BrickInfo &NI = sm.info[cur ^ 1];
+        const BrickInfo &NI = sm.info[nxt];
         const int64_t b = I.brick;
         if (b >= total_bricks) break;
         const BrickGeom &G = kBatched ? I.geom : p.G;
@@ -660,8 +665,11 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
         const int64_t lo_n = NI.lo, cnt_n = next_ok ? NI.hi - NI.lo : 0;
         if (cnt == 0 && !p.fresh) {
             have_pref = false;
-            cur ^= 1;
-            __syncthreads();  // everyone has read the brick records before they are rewritten
+            if (taker) take_brick<kBatched>(p, overflow, sm.info[aft]);  // read by no one now
+            const int c = cur;
+            cur = nxt;
+            nxt = aft;
+            aft = c;
             continue;
         }
         // the warp's first group (group `warp`): loaded ahead, or its pieces now
@@ -686,6 +694,9 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
         }
         if (!have_pref && j < cnt) load_record(p.segs, static_cast<int64_t>(pc & 0xffffffffull), rec);
         __syncthreads();
+        // the brick after the next one: its ticket is taken while the CTA walks this
+        // one (its ring slot held the brick before this one, read by no one now)
+        if (taker) take_brick<kBatched>(p, overflow, sm.info[aft]);
         // brick-local bit index of (x, y, z): (x - X0) + B0 (y - Y0) + B0 B1 (z - Z0),
         // kept modulo 2^32 while stepping (only the local value is ever used)
         const uint32_t origin = static_cast<uint32_t>(X0) + static_cast<uint32_t>(Y0) * bw +
@@ -743,7 +754,10 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
             if (mask != nullptr) merge_brick(sm.bits, G, X0, Y0, Z0, mask, p.fresh != 0);
             __syncthreads();
         }
-        cur ^= 1;
+        const int c = cur;
+        cur = nxt;
+        nxt = aft;
+        aft = c;
     }
     if (async_store && t == 0) bulk_wait_all();  // copies complete before the CTA's memory goes
 }

@@ -12,12 +12,15 @@
 // minimum for 256 bytes). The finished slice leaves with one TMA bulk copy from
 // shared to global memory (cp.async.bulk), so the SM issues no load/store
 // instructions for the write-out and no CTA-wide barrier: each warp runs on its
-// own, taking chunks of slices from a global work counter (one atomic per chunk).
+// own, taking chunks of slices from a global work counter (one atomic and one
+// search in the offsets per chunk; 1 to 16 slices per chunk, about eight chunks
+// per warp, so that short lists still spread evenly).
 //
 // Segment records and offsets are staged per warp in windows of 32 segments
-// (plain coalesced loads into the warp's shared memory); a slice that spans more
-// segments is processed in several windows, each lane keeping its stepping state
-// across them.
+// (plain coalesced loads into the warp's shared memory) and kept for the next
+// slice of the chunk while at least 16 of the window's segments lie ahead of
+// it; a slice that spans more segments is processed in several windows, each
+// lane keeping its stepping state across them.
 #pragma once
 
 #include <cstdint>
@@ -34,7 +37,8 @@ constexpr int kListSlice = 32 * kListRun;      // voxels per warp slice (1056, a
 constexpr int kListWarps = 4;                  // warps per CTA
 constexpr int kListThreads = 32 * kListWarps;
 constexpr int kListWin = 32;                   // segments per staged window
-constexpr int kListChunkSlices = 4;            // slices per fetch from the work counter
+constexpr int kListChunkMax = 16;              // slices per fetch from the work counter, at most
+constexpr int kListChunksPerWarp = 8;          // chunks per warp aimed at (for balance)
 static_assert(kListSlice % 4 == 0, "slices must keep 16-byte aligned list addresses");
 
 struct ListParams {
@@ -111,7 +115,10 @@ __global__ void __launch_bounds__(kListThreads) k_list(ListParams p)
     if (!s_go) return;
     const int64_t V = s_V;
     PackT *const list = static_cast<PackT *>(p.list);
-    constexpr int64_t kChunk = static_cast<int64_t>(kListChunkSlices) * kListSlice;
+    const int64_t n_slices = (V + kListSlice - 1) / kListSlice;
+    const int64_t n_warps = static_cast<int64_t>(gridDim.x) * kListWarps;
+    const int64_t chunk_slices = max64(1, min64(kListChunkMax, n_slices / (n_warps * kListChunksPerWarp)));
+    const int64_t kChunk = chunk_slices * kListSlice;
     bool pending = false;  // lane 0: a bulk store may still be reading this warp's stage
 
     while (true) {
@@ -122,6 +129,8 @@ __global__ void __launch_bounds__(kListThreads) k_list(ListParams p)
         if (g_begin >= V) break;
         const int64_t g_end = min64(g_begin + kChunk, V);
         int64_t s = warp_find_segment(p.offsets, p.n, g_begin, lane);
+        int64_t ws_keep = -1;   // the staged window of the previous slice
+        int32_t wcnt_keep = 0;
         for (int64_t g = g_begin; g < g_end; g += kListSlice) {
             const int32_t len = static_cast<int32_t>(min64(kListSlice, g_end - g));
             const int32_t my0 = kListRun * lane;
@@ -135,11 +144,13 @@ __global__ void __launch_bounds__(kListThreads) k_list(ListParams p)
             int32_t kin = 0;    // step at which to enter it
             bool live = false;  // stepping state valid for cur
             bool ended = false; // the last voxel written ended its segment
-            int64_t ws = s;     // first segment of the window
+            // keep the previous slice's window while 16 of its segments lie ahead
+            bool staged = ws_keep >= 0 && s >= ws_keep && s + kListWin / 2 <= ws_keep + wcnt_keep;
+            int64_t ws = staged ? ws_keep : s;  // first segment of the window
             while (__any_sync(0xffffffffu, done < rlen)) {
-                const int32_t wcnt = static_cast<int32_t>(min64(kListWin, p.n - ws));
+                const int32_t wcnt = staged ? wcnt_keep : static_cast<int32_t>(min64(kListWin, p.n - ws));
                 __syncwarp();  // every lane is done with the previous window
-                {
+                if (!staged) {
                     const int64_t sj = ws + lane;
                     if (lane < wcnt) {
                         const int2 *r = reinterpret_cast<const int2 *>(p.segs + 6 * sj);
@@ -189,8 +200,13 @@ __global__ void __launch_bounds__(kListThreads) k_list(ListParams p)
                         }
                     }
                 }
-                ws += wcnt;
-                if (wcnt == 0) break;  // unreachable for a consistent scan; keeps the loop finite
+                ws_keep = ws;
+                wcnt_keep = wcnt;
+                staged = false;  // a further round stages the next window
+                if (__any_sync(0xffffffffu, done < rlen)) {
+                    ws += wcnt;
+                    if (wcnt == 0) break;  // unreachable for a consistent scan; keeps the loop finite
+                }
             }
             // the next slice starts in the segment of this slice's last voxel, or
             // the next one if that voxel ended its segment
