@@ -1014,6 +1014,13 @@ def run_ours(args):
     if args.only and args.tuning:
         knobs = [int(x) for x in args.tuning.split(",")] + [0]
         vox.vox_set_tuning(*knobs[:4])
+    if args.only == "config2":  # the fixed-length batch's block alone (profiler runs)
+        w2 = workloads.config2()
+        sb2 = SceneBench("config2", w2, vox.OUT_LIST32, dev, tune=not args.no_tune and not args.tuning,
+                         tuning_arg=args.tuning)
+        t2 = sb2.run(args.steps, args.warmup, flush, stream)
+        print(json.dumps(sb2.summary(t2)), flush=True)
+        return 0
     if args.only in ("list", "volume"):  # one phase of a smaller log-uniform batch (profiler runs)
         print(json.dumps(measure_phase(args.only, args.segments, args.edge, args.steps, dev, stream, flush)),
               flush=True)
@@ -1120,7 +1127,7 @@ def main():
     ap.add_argument("--no-config2", action="store_true")
     ap.add_argument("--no-latency", action="store_true")
     ap.add_argument("--no-atomics", action="store_true")
-    ap.add_argument("--only", choices=["atomics", "list", "volume"], default=None,
+    ap.add_argument("--only", choices=["atomics", "list", "volume", "config2"], default=None,
                     help="run one section alone and print it (list / volume: one phase of a smaller log-uniform batch)")
     ap.add_argument("--segments", type=int, default=1 << 19, help="--only list/volume: segments")
     ap.add_argument("--edge", type=int, default=2048, help="--only list/volume: volume edge")
