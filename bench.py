@@ -1021,6 +1021,13 @@ def run_ours(args):
         t2 = sb2.run(args.steps, args.warmup, flush, stream)
         print(json.dumps(sb2.summary(t2)), flush=True)
         return 0
+    if args.only == "batched":  # the 256-scene batched-vs-plain block alone (profiler runs)
+        print(json.dumps({"batched_vs_plain": measure_batched(args.steps, dev, tune=not args.tuning)}), flush=True)
+        return 0
+    if args.only == "euclid":  # the Euclidean-N variant on the fixed-length batch alone (profiler runs)
+        print(json.dumps({"euclid_variant": measure_euclid(workloads.config2(), dev, stream, flush, args.steps)}),
+              flush=True)
+        return 0
     if args.only in ("list", "volume"):  # one phase of a smaller log-uniform batch (profiler runs)
         print(json.dumps(measure_phase(args.only, args.segments, args.edge, args.steps, dev, stream, flush)),
               flush=True)
@@ -1127,7 +1134,7 @@ def main():
     ap.add_argument("--no-config2", action="store_true")
     ap.add_argument("--no-latency", action="store_true")
     ap.add_argument("--no-atomics", action="store_true")
-    ap.add_argument("--only", choices=["atomics", "list", "volume", "config2"], default=None,
+    ap.add_argument("--only", choices=["atomics", "list", "volume", "config2", "euclid", "batched"], default=None,
                     help="run one section alone and print it (list / volume: one phase of a smaller log-uniform batch)")
     ap.add_argument("--segments", type=int, default=1 << 19, help="--only list/volume: segments")
     ap.add_argument("--edge", type=int, default=2048, help="--only list/volume: volume edge")
