@@ -807,15 +807,24 @@ vox_status launch_euclid_runs(const EuclidParams &p, cudaStream_t stream)
     return cudaGetLastError() == cudaSuccess ? VOX_OK : VOX_ERR_CUDA;
 }
 
+// The warp walk over groups of 32 runs: a persistent grid (SMs x CTAs per SM,
+// no more CTAs than the groups fill), warps striding over the groups.
+template <bool kWrite, int OUT, bool LIN64>
+vox_status launch_euclid_warp(const EuclidParams &p, cudaStream_t stream)
+{
+    const void *k = reinterpret_cast<const void *>(k_euclid_warp<kWrite, OUT, LIN64>);
+    int grid = grid_ctas(k, 32 * kEuclidWarps, 0);
+    if (grid <= 0) return VOX_ERR_CUDA;
+    const int64_t groups = (p.n_runs + 31) / 32;
+    grid = static_cast<int>(std::min<int64_t>(grid, (groups + kEuclidWarps - 1) / kEuclidWarps));
+    k_euclid_warp<kWrite, OUT, LIN64><<<static_cast<unsigned>(grid), 32 * kEuclidWarps, 0, stream>>>(p);
+    return cudaGetLastError() == cudaSuccess ? VOX_OK : VOX_ERR_CUDA;
+}
+
 template <int OUT, bool LIN64>
 vox_status launch_euclid_list(const EuclidParams &p, cudaStream_t stream)
 {
-    const int sms = sm_count();
-    if (sms <= 0) return VOX_ERR_CUDA;
-    const int64_t want = (p.n_runs + 255) / 256;
-    const unsigned blocks = static_cast<unsigned>(std::min<int64_t>(want, static_cast<int64_t>(sms) * 8));
-    k_euclid_list<OUT, LIN64><<<blocks, 256, 0, stream>>>(p);
-    return cudaGetLastError() == cudaSuccess ? VOX_OK : VOX_ERR_CUDA;
+    return launch_euclid_warp<true, OUT, LIN64>(p, stream);
 }
 
 // Count + scan of the samples (and the brick binning's counts when the workspace
@@ -856,7 +865,7 @@ vox_status launch_euclid(const vox_segment *segs, int64_t n, vox_dims dims, void
     // the segment offsets and the plan; a volume alone goes without them
     const bool positions = count_only || seg_off != nullptr || (flags & (VOX_OUT_LIST32 | VOX_OUT_LIST64));
     if (positions) {
-        if (vox_status e = launch_euclid_runs<false, 0, false>(p, stream)) return e;
+        if (vox_status e = launch_euclid_warp<false, 0, false>(p, stream)) return e;
         ScanParams sp{};
         sp.counts_in = p.run_count;
         sp.n = E.n_runs;
