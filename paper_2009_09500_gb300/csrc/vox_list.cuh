@@ -16,6 +16,14 @@
 // search in the offsets per chunk; 1 to 16 slices per chunk, about eight chunks
 // per warp, so that short lists still spread evenly).
 //
+// A slice with few segment ends inside it (kListFlatMax at most, counted in the
+// staged window) is walked in one loop over each lane's run: a voxel that ends
+// its segment is followed in place by the next segment's first voxel (entered at
+// k = 0, no division), so that the lanes stay in step and the few that cross a
+// segment end hold the others up only for that entry. A slice with many ends is
+// walked part by part (one part per segment), so that the lanes' entries happen
+// together instead of one after another.
+//
 // Segment records and offsets are staged per warp in windows of 32 segments
 // (plain coalesced loads into the warp's shared memory) and kept for the next
 // slice of the chunk while at least 16 of the window's segments lie ahead of
@@ -39,6 +47,7 @@ constexpr int kListThreads = 32 * kListWarps;
 constexpr int kListWin = 32;                   // segments per staged window
 constexpr int kListChunkMax = 16;              // slices per fetch from the work counter, at most
 constexpr int kListChunksPerWarp = 8;          // chunks per warp aimed at (for balance)
+constexpr int kListFlatMax = 12;                // segment ends per slice up to which runs cross them in place
 static_assert(kListSlice % 4 == 0, "slices must keep 16-byte aligned list addresses");
 
 struct ListParams {
@@ -162,6 +171,12 @@ __global__ void __launch_bounds__(kListThreads) k_list(ListParams p)
                     if (lane == 0 && wcnt == kListWin) sm.offs[kListWin] = __ldg(p.offsets + ws + kListWin);
                 }
                 __syncwarp();
+                // segment ends inside the slice that this window holds: with few, the
+                // lanes cross them in one loop over their runs (entering the next
+                // segment in place); with many, a loop per segment part keeps the
+                // entries together
+                const bool flat = __popc(__ballot_sync(0xffffffffu, lane >= 1 && lane <= wcnt && sm.offs[lane] > g &&
+                                                                         sm.offs[lane] < g + len)) <= kListFlatMax;
                 if (done < rlen) {
                     if (cur < 0) {  // the segment of the run's first voxel, if in this window
                         const int64_t r = g + my0;
@@ -171,32 +186,65 @@ __global__ void __launch_bounds__(kListThreads) k_list(ListParams p)
                             kin = static_cast<int32_t>(r - sm.offs[j]);
                         }
                     }
-                    PackT *o = sm.stage + my0 + done;
-                    while (cur >= 0 && done < rlen && cur < ws + wcnt) {
-                        if (!live) {
-                            st.enter(sm.recs + 6 * static_cast<int32_t>(cur - ws), kin, 0u, 0u);
-                            live = true;
+                    if (flat) {
+                        if (cur >= 0 && done < rlen && cur < ws + wcnt) {
+                            if (!live) {
+                                st.enter(sm.recs + 6 * static_cast<int32_t>(cur - ws), kin, 0u, 0u);
+                                live = true;
+                            }
+                            int32_t left = st.left;  // voxels after this one in its segment
+                            int32_t u = done;
+#pragma unroll 4
+                            for (; u < rlen; ++u) {
+                                sm.stage[my0 + u] = st.P;
+                                ended = (left == 0);
+                                if (!ended) {
+                                    --left;
+                                    st.template step<true, false>();
+                                    continue;
+                                }
+                                if (u + 1 == rlen) continue;  // the run ends with its segment
+                                ++cur;                        // the run goes on in the next segment
+                                kin = 0;
+                                live = false;
+                                if (cur >= ws + wcnt) {       // ... which a later window holds
+                                    ++u;
+                                    break;
+                                }
+                                st.enter(sm.recs + 6 * static_cast<int32_t>(cur - ws), 0, 0u, 0u);
+                                live = true;
+                                left = st.left;
+                            }
+                            done = u;
                         }
-                        const int32_t m = min(st.left + 1, rlen - done);
-                        ended = (m == st.left + 1);
-                        int32_t e = 0;
-                        for (; e + 4 <= m; e += 4) {
+                    } else {
+                        PackT *o = sm.stage + my0 + done;
+                        while (cur >= 0 && done < rlen && cur < ws + wcnt) {
+                            if (!live) {
+                                st.enter(sm.recs + 6 * static_cast<int32_t>(cur - ws), kin, 0u, 0u);
+                                live = true;
+                            }
+                            const int32_t m = min(st.left + 1, rlen - done);
+                            ended = (m == st.left + 1);
+                            int32_t e = 0;
+                            for (; e + 4 <= m; e += 4) {
 #pragma unroll
-                            for (int v = 0; v < 4; ++v) {
-                                o[v] = st.P;
+                                for (int v = 0; v < 4; ++v) {
+                                    o[v] = st.P;
+                                    st.template step<true, false>();
+                                }
+                                o += 4;
+                            }
+                            for (; e < m; ++e) {
+                                *o++ = st.P;
                                 st.template step<true, false>();
                             }
-                            o += 4;
-                        }
-                        for (; e < m; ++e) {
-                            *o++ = st.P;
-                            st.template step<true, false>();
-                        }
-                        done += m;
-                        if (done < rlen) {  // the run goes on in the next segment
-                            ++cur;
-                            kin = 0;
-                            live = false;
+                            done += m;
+                            if (done < rlen) {  // the run goes on in the next segment
+                                ++cur;
+                                kin = 0;
+                                live = false;
+                            }
                         }
                     }
                 }
