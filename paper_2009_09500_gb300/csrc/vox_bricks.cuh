@@ -521,7 +521,8 @@ __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bu
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // Merge a brick's shared bitmap into the volume. Brick row (ly, lz) holds bxw
-// words that are contiguous in the volume; a warp covers 32 consecutive words.
+// words that are contiguous in the volume; a warp covers 32 consecutive words
+// (or 32 consecutive 16-byte units, when rows and the volume allow them).
 // OR mode reads and writes only touched words; fresh mode writes every word of
 // the brick inside the volume (zeros included) and reads none. Eight
 // independent loads per thread are issued before the stores, so DRAM latency is
@@ -530,8 +531,51 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 __device__ __forceinline__ void merge_brick(const uint32_t *bits, const BrickGeom &G, int32_t X0, int32_t Y0,
                                             int32_t Z0, uint32_t *mask, bool fresh)
 {
-    constexpr int kGroup = 8;
     const int t = threadIdx.x;
+    if ((G.bxw & 3) == 0 && (G.row_words & 3) == 0 && (reinterpret_cast<uintptr_t>(mask) & 15u) == 0) {
+        // 16-byte units (a brick row holds bxw / 4 of them): the brick's first word
+        // in a row, X0 / 32, is a multiple of bxw and the volume's rows are whole
+        // 16-byte units, so every unit is aligned and lies in or beyond the row
+        // as a whole; four units per thread in flight
+        constexpr int kGroup4 = 4;
+        const uint4 *b4 = reinterpret_cast<const uint4 *>(bits);
+        uint4 *m4 = reinterpret_cast<uint4 *>(mask);
+        const int32_t units = G.words >> 2;
+        const int32_t log_bxu = G.log_bxw - 2;
+        const int32_t row_units = G.row_words >> 2;
+        const int32_t x_unit = X0 / 128;
+        for (int q0 = 0; q0 < units; q0 += kGroup4 * kBrickThreads) {
+            uint4 v[kGroup4], old[kGroup4];
+            int64_t gu[kGroup4];
+            bool wr[kGroup4];
+#pragma unroll
+            for (int e = 0; e < kGroup4; ++e) {
+                const int q = q0 + e * kBrickThreads + t;
+                v[e] = make_uint4(0u, 0u, 0u, 0u);
+                gu[e] = 0;
+                wr[e] = false;
+                if (q < units) {
+                    const uint4 b = b4[q];
+                    const int32_t row = q >> log_bxu, col = q & ((1 << log_bxu) - 1);
+                    const int32_t y = Y0 + (row & (G.B[1] - 1)), z = Z0 + (row >> G.log_b1);
+                    if ((fresh || (b.x | b.y | b.z | b.w) != 0u) && y < G.dim[1] && z < G.dim[2] &&
+                        x_unit + col < row_units) {
+                        v[e] = b;
+                        wr[e] = true;
+                        gu[e] = x_unit + col + static_cast<int64_t>(row_units) * (y + static_cast<int64_t>(G.dim[1]) * z);
+                    }
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < kGroup4; ++e) old[e] = (wr[e] && !fresh) ? m4[gu[e]] : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+            for (int e = 0; e < kGroup4; ++e)
+                if (wr[e])
+                    m4[gu[e]] = make_uint4(old[e].x | v[e].x, old[e].y | v[e].y, old[e].z | v[e].z, old[e].w | v[e].w);
+        }
+        return;
+    }
+    constexpr int kGroup = 8;
     for (int q0 = 0; q0 < G.words; q0 += kGroup * kBrickThreads) {
         uint32_t v[kGroup], old[kGroup];
         int64_t gw[kGroup];
