@@ -17,12 +17,14 @@
 // per warp, so that short lists still spread evenly).
 //
 // A slice with few segment ends inside it (kListFlatMax at most, counted in the
-// staged window) is walked in one loop over each lane's run: a voxel that ends
-// its segment is followed in place by the next segment's first voxel (entered at
-// k = 0, no division), so that the lanes stay in step and the few that cross a
-// segment end hold the others up only for that entry. A slice with many ends is
-// walked part by part (one part per segment), so that the lanes' entries happen
-// together instead of one after another.
+// staged window) is walked by the lanes in step over their runs: four voxels at
+// a time while no lane is within four voxels of its segment's or run's end (one
+// vote per four voxels), else one voxel, a voxel that ends its segment being
+// followed in place by the next segment's first voxel (entered at k = 0, no
+// division); the few lanes that cross a segment end hold the others up only for
+// that entry. A slice with many ends is walked part by part (one part per
+// segment), so that the lanes' entries happen together instead of one after
+// another.
 //
 // Segment records and offsets are staged per warp in windows of 32 segments
 // (plain coalesced loads into the warp's shared memory) and kept for the next
@@ -177,74 +179,93 @@ __global__ void __launch_bounds__(kListThreads) k_list(ListParams p)
                 // entries together
                 const bool flat = __popc(__ballot_sync(0xffffffffu, lane >= 1 && lane <= wcnt && sm.offs[lane] > g &&
                                                                          sm.offs[lane] < g + len)) <= kListFlatMax;
-                if (done < rlen) {
-                    if (cur < 0) {  // the segment of the run's first voxel, if in this window
-                        const int64_t r = g + my0;
-                        if (r < sm.offs[wcnt]) {
-                            const int32_t j = find_in_window32(sm.offs, wcnt, r);
-                            cur = ws + j;
-                            kin = static_cast<int32_t>(r - sm.offs[j]);
-                        }
+                if (done < rlen && cur < 0) {  // the segment of the run's first voxel, if in this window
+                    const int64_t r = g + my0;
+                    if (r < sm.offs[wcnt]) {
+                        const int32_t j = find_in_window32(sm.offs, wcnt, r);
+                        cur = ws + j;
+                        kin = static_cast<int32_t>(r - sm.offs[j]);
                     }
-                    if (flat) {
-                        if (cur >= 0 && done < rlen && cur < ws + wcnt) {
-                            if (!live) {
-                                st.enter(sm.recs + 6 * static_cast<int32_t>(cur - ws), kin, 0u, 0u);
-                                live = true;
-                            }
-                            int32_t left = st.left;  // voxels after this one in its segment
-                            int32_t u = done;
-#pragma unroll 4
-                            for (; u < rlen; ++u) {
-                                sm.stage[my0 + u] = st.P;
-                                ended = (left == 0);
-                                if (!ended) {
-                                    --left;
-                                    st.template step<true, false>();
-                                    continue;
-                                }
-                                if (u + 1 == rlen) continue;  // the run ends with its segment
-                                ++cur;                        // the run goes on in the next segment
-                                kin = 0;
-                                live = false;
-                                if (cur >= ws + wcnt) {       // ... which a later window holds
-                                    ++u;
-                                    break;
-                                }
-                                st.enter(sm.recs + 6 * static_cast<int32_t>(cur - ws), 0, 0u, 0u);
-                                live = true;
-                                left = st.left;
-                            }
-                            done = u;
-                        }
-                    } else {
-                        PackT *o = sm.stage + my0 + done;
-                        while (cur >= 0 && done < rlen && cur < ws + wcnt) {
-                            if (!live) {
-                                st.enter(sm.recs + 6 * static_cast<int32_t>(cur - ws), kin, 0u, 0u);
-                                live = true;
-                            }
-                            const int32_t m = min(st.left + 1, rlen - done);
-                            ended = (m == st.left + 1);
-                            int32_t e = 0;
-                            for (; e + 4 <= m; e += 4) {
+                }
+                // the flat walk's votes need every lane: flat is the same for the whole warp
+                if (flat) {
+                    // the lanes walk in step: four voxels at once while no walking
+                    // lane is within four voxels of its segment's or run's end,
+                    // else one voxel, a segment end crossed in place
+                    bool go = cur >= 0 && done < rlen && cur < ws + wcnt;  // walks in this window
+                    if (go && !live) {
+                        st.enter(sm.recs + 6 * static_cast<int32_t>(cur - ws), kin, 0u, 0u);
+                        live = true;
+                    }
+                    int32_t left = go ? st.left : 0;  // voxels after this one in its segment
+                    int32_t u = done;
+                    while (__any_sync(0xffffffffu, go)) {
+                        if (__all_sync(0xffffffffu, !go || (left >= 4 && u + 4 <= rlen))) {
+                            if (go) {
 #pragma unroll
                                 for (int v = 0; v < 4; ++v) {
-                                    o[v] = st.P;
+                                    sm.stage[my0 + u + v] = st.P;
                                     st.template step<true, false>();
                                 }
-                                o += 4;
+                                u += 4;
+                                left -= 4;
+                                ended = false;
+                                go = u < rlen;
                             }
-                            for (; e < m; ++e) {
-                                *o++ = st.P;
+                            continue;
+                        }
+                        if (go) {
+                            sm.stage[my0 + u] = st.P;
+                            ended = (left == 0);
+                            ++u;
+                            if (!ended) {
+                                --left;
                                 st.template step<true, false>();
-                            }
-                            done += m;
-                            if (done < rlen) {  // the run goes on in the next segment
+                                go = u < rlen;
+                            } else if (u == rlen) {  // the run ends with its segment
+                                go = false;
+                            } else {                 // the run goes on in the next segment
                                 ++cur;
                                 kin = 0;
                                 live = false;
+                                if (cur >= ws + wcnt) {  // ... which a later window holds
+                                    go = false;
+                                } else {
+                                    st.enter(sm.recs + 6 * static_cast<int32_t>(cur - ws), 0, 0u, 0u);
+                                    live = true;
+                                    left = st.left;
+                                }
                             }
+                        }
+                    }
+                    done = u;
+                } else if (done < rlen) {
+                    PackT *o = sm.stage + my0 + done;
+                    while (cur >= 0 && done < rlen && cur < ws + wcnt) {
+                        if (!live) {
+                            st.enter(sm.recs + 6 * static_cast<int32_t>(cur - ws), kin, 0u, 0u);
+                            live = true;
+                        }
+                        const int32_t m = min(st.left + 1, rlen - done);
+                        ended = (m == st.left + 1);
+                        int32_t e = 0;
+                        for (; e + 4 <= m; e += 4) {
+#pragma unroll
+                            for (int v = 0; v < 4; ++v) {
+                                o[v] = st.P;
+                                st.template step<true, false>();
+                            }
+                            o += 4;
+                        }
+                        for (; e < m; ++e) {
+                            *o++ = st.P;
+                            st.template step<true, false>();
+                        }
+                        done += m;
+                        if (done < rlen) {  // the run goes on in the next segment
+                            ++cur;
+                            kin = 0;
+                            live = false;
                         }
                     }
                 }
