@@ -97,6 +97,23 @@ def assert_clean(results, expect_jobs=None):
     return nonzero
 
 
+def assert_same_list_by_warp_slices(segs, dims, ws, status, lst):
+    """The list alone by warp slices (launch tuning 32,0,0,2: the one the
+    benchmark's tuner picks for long segments) equals, element by element, the
+    list `lst` that the oracle checks in full."""
+    lst2 = torch.empty_like(lst)
+    try:
+        vox.vox_set_tuning(32, 0, 0, 2)
+        vox.vox_generate(segs, dims, ws, status, lst2, None, L64, capacity=lst.numel())
+        torch.cuda.synchronize()
+    finally:
+        vox.vox_reset_tuning()
+    assert int(status.item()) == 0
+    assert torch.equal(lst2, lst), "the warp-slice list differs"
+    del lst2
+    torch.cuda.empty_cache()
+
+
 def test_config3_full_size_exact(pool):
     """4M log-uniform segments, 4096^3: whole list64 and both 8 GiB volumes."""
     w = workloads.config3()
@@ -124,6 +141,7 @@ def test_config3_full_size_exact(pool):
     vox.vox_generate(segs, w.dims, ws, status, lst, mask_atomic)
     torch.cuda.synchronize()
     assert int(status.item()) == 0
+    assert_same_list_by_warp_slices(segs, w.dims, ws, status, lst)
     # the fresh volume by bricks (the benchmarked path) over stale bits
     ws0 = torch.empty(vox.vox_workspace_size_volume(n, w.dims, 0), dtype=torch.uint8, device="cuda")
     V2, P = vox.vox_plan(segs, w.dims, ws0, status)
@@ -170,6 +188,7 @@ def test_total_beyond_2_to_31_exact(pool):
     torch.cuda.synchronize()
     assert int(status.item()) == 0
     assert np.array_equal(d_off.cpu().numpy(), off)
+    assert_same_list_by_warp_slices(segs, dims, ws, status, lst)
     segs_buf = pool.buf(segs_np)
     try:
         submit_list(pool, segs_buf, off, lst, True, "2^31")
@@ -191,6 +210,20 @@ def test_batched_config4_all_scenes_exact(pool):
     b.run()
     torch.cuda.synchronize()
     assert int(b.status.item()) == 0, vox.strerror(int(b.status.item()))
+    # the same batch under the launch tuning its tuner picks (the list by warp
+    # slices): outputs equal to these, which the oracle checks in full below
+    lst_ref = b.lst.clone()
+    masks_ref = [m.clone() for m in b.masks]
+    try:
+        vox.vox_set_tuning(32, 0, 0, 2)
+        b.run()
+        torch.cuda.synchronize()
+    finally:
+        vox.vox_reset_tuning()
+    assert int(b.status.item()) == 0, vox.strerror(int(b.status.item()))
+    assert torch.equal(b.lst, lst_ref), "the batched list by warp slices differs"
+    assert all(torch.equal(m, r) for m, r in zip(b.masks, masks_ref))
+    del lst_ref, masks_ref
     O = get_oracle()
     base = b.scene_base.cpu().numpy()
     per_scene = np.array([O.total(s.segs) for s in scenes])
