@@ -423,7 +423,8 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(BinParams p)
     // geometry, writes only the slot counts, and skips segments with endpoints
     // outside the volume (reported by the count kernel)
     // a batch reads the scene map and numbering, valid only without an error
-    if (kBatched && ld_volatile_i32(p.status) != 0) return;
+    // (decided by the whole warp: the walk's shuffles and votes need every lane)
+    if (kBatched && __any_sync(0xffffffffu, ld_volatile_i32(p.status) != 0)) return;
     bin_loop<kEuclid, kBatched>(p, [&](int64_t slot, int64_t, int32_t, int32_t) {
         atomicAdd(p.brick_count + slot, 1);
     });
@@ -436,7 +437,9 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(BinParams p)
 template <bool kEuclid, bool kBatched = false>
 __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(BinParams p)
 {
-    if (ld_volatile_i32(p.status) != 0) return;
+    // an earlier error: write nothing (decided by the whole warp, whose walk takes
+    // shuffles and votes; the status word may be set by a kernel on another stream)
+    if (__any_sync(0xffffffffu, ld_volatile_i32(p.status) != 0)) return;
     if (__ldg(p.brick_off + p.G.n_slots) > p.capacity) return;  // the volume falls back to atomics
     constexpr int kBatch = 4;
     int64_t bb[kBatch];
@@ -671,7 +674,9 @@ __global__ void __launch_bounds__(kBrickThreads) k_brick_volume(BrickParams p, c
     const int t = threadIdx.x;
     const int lane = t & 31;
     const int warp = t >> 5;
-    if (ld_volatile_i32(p.status) != 0) return;
+    // an earlier error: write nothing, decided by the whole CTA (the status word may
+    // be set meanwhile by a kernel on another stream, and the CTA meets at barriers)
+    if (__syncthreads_or(ld_volatile_i32(p.status) != 0)) return;
     // pieces that did not fit: the gated atomics pass ORs the voxels in (after a
     // fresh volume has been cleared here, brick by brick)
     const bool overflow = __ldg(p.brick_off + p.G.n_slots) > p.capacity;

@@ -217,7 +217,8 @@ __global__ void __launch_bounds__(32 * kEuclidWarps, kWrite ? 1 : 12) k_euclid_w
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     Smem &sm = smem_all[wib];
-    if (ld_volatile_i32(p.status) != 0) return;  // an earlier error: write nothing
+    // an earlier error: write nothing (decided by the whole warp, which votes later)
+    if (__any_sync(0xffffffffu, ld_volatile_i32(p.status) != 0)) return;
     if (kList && __ldg(p.run_off + p.n_runs) > p.capacity) {
         if (blockIdx.x == 0 && threadIdx.x == 0) set_status(p.status, kStCapacity);
         return;

@@ -800,7 +800,7 @@ __global__ void __launch_bounds__(kSceneBrickThreads) k_scene_bricks(const Scene
     __shared__ int64_t s_sum[kSceneBrickThreads];
     __shared__ int32_t s_bad;
     const int t = threadIdx.x;
-    if (ld_volatile_i32(status) != 0) return;  // uniform: the table was refused
+    if (__syncthreads_or(ld_volatile_i32(status) != 0)) return;  // the table was refused (the CTA agrees)
     if (t == 0) s_bad = 0;
     __syncthreads();
     const int32_t per = (n_scenes + kSceneBrickThreads - 1) / kSceneBrickThreads;
