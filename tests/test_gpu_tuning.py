@@ -134,3 +134,57 @@ def test_warp_slice_list_bit_exact(wide):
         assert (lst.cpu().numpy() == -1).all(), "nothing may be written on a capacity error"
     finally:
         vox.vox_reset_tuning()
+
+
+def _seg_along_x(x0, y, z, length):
+    """A segment of `length` voxels along x."""
+    return [x0, y, z, x0 + length - 1, y, z]
+
+
+@pytest.mark.parametrize("wide", [False, True])
+@pytest.mark.parametrize("case", ["one_short", "few_long_ragged", "whole_slices", "long_then_tiny"])
+def test_warp_slice_list_few_segment_ends(case, wide):
+    """Lists by warp slices where slices have few segment ends (the lanes walk in
+    step, crossing segment ends in place): one 100-voxel segment (one slice, most
+    lanes without voxels), a few long segments ending mid-slice, a list of whole
+    slices exactly (5 x 1056 voxels), long segments followed by one-voxel ones (a
+    slice's window ending inside it); the whole list against the oracle, nothing
+    written past it."""
+    from paper_2009_09500_gb300 import build
+
+    build.build_library()
+    edge = 4096 if wide else 1024
+    rng = np.random.default_rng(41)
+    if case == "one_short":
+        segs_np = np.array([_seg_along_x(3, 5, 7, 100)], np.int32)
+    elif case == "few_long_ragged":
+        segs_np = workloads._segments_from_major(rng, np.array([edge - 1, 777, edge // 2 + 3, 1234 % edge]), edge)
+    elif case == "whole_slices":
+        segs_np = np.array([_seg_along_x(0, 1, 2, 1000), _seg_along_x(0, 3, 4, 1000), _seg_along_x(0, 5, 6, 1000),
+                            _seg_along_x(0, 7, 8, 1000), _seg_along_x(0, 9, 10, 1000), _seg_along_x(0, 11, 12, 280)],
+                           np.int32)
+        assert int(np.abs(segs_np[:, 3] - segs_np[:, 0]).sum() + len(segs_np)) == 5 * 1056
+    else:
+        longs = workloads._segments_from_major(rng, np.full(40, edge - 1, np.int64), edge)
+        tiny = workloads._segments_from_major(rng, np.zeros(3000, np.int64), edge)
+        segs_np = np.concatenate([longs, tiny, longs[:3]])
+    segs_np = np.ascontiguousarray(segs_np.astype(np.int32))
+    dims = (edge, edge, edge)
+    O = get_oracle()
+    want = O.list64(segs_np) if wide else O.list32(segs_np)
+    V = len(want)
+    segs = torch.from_numpy(segs_np).cuda()
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ws = torch.empty(vox.vox_workspace_size(segs.shape[0]), dtype=torch.uint8, device="cuda")
+    dt = torch.int64 if wide else torch.int32
+    lst = torch.full((V + 64,), -1, dtype=dt, device="cuda")
+    try:
+        vox.vox_set_tuning(32, 0, 0, 2)
+        vox.vox_generate(segs, dims, ws, st, lst, None, vox.OUT_LIST64 if wide else vox.OUT_LIST32, capacity=V)
+        torch.cuda.synchronize()
+    finally:
+        vox.vox_reset_tuning()
+    assert int(st.item()) == 0
+    got = lst.cpu().numpy().view(want.dtype)
+    assert np.array_equal(got[:V], want)
+    assert (got[V:] == np.array(-1, dtype=np.int64).astype(want.dtype)).all(), "written past the list"
