@@ -186,3 +186,15 @@ def test_bricks_volume_only_with_offsets_and_capacity_error():
     r = run_euclid(w.segs, w.dims, L32 | BM, capacity=Vd - 1, pieces="plan")
     assert r["status"] == vox.ERR_CAPACITY
     assert (r["list"] == SENT).all() and (r["mask"] == 0).all()
+
+
+def test_long_runs_many_row_flushes():
+    """About 2.4e8 samples in 2000 long segments: runs of about 230 samples (the
+    run slots are fixed by n), so each lane's row fills and is flushed several times
+    per run and a warp's 32 runs lie in one or two segments; whole 64-bit list and
+    segment offsets against the oracle."""
+    rng = np.random.default_rng(12)
+    edge = 1 << 21
+    segs = workloads._segments_from_major(rng, np.full(2000, 99_999, np.int64), edge).astype(np.int32)
+    r = check(segs, (edge, edge, edge), L64)
+    assert r["Vd"] > 2000 * 100_000
